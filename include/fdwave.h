@@ -1,0 +1,222 @@
+/*
+ * fdwave.h -- C ABI of libfdwave, a GB300 (sm_103a) finite-difference solver
+ * for the damped, variable-velocity acoustic wave equation
+ *
+ *     m u_tt + eta u_t - lap(u) = q                     (arXiv 1609.03361, Sec. 5, Eq. 3)
+ *
+ * with explicit second-order time stepping, central space orders 2..16, an
+ * absorbing damping layer, multilinear source injection / receiver sampling
+ * (Sec. 5.2, Listing 8), the adjoint propagator (Sec. 5.1, Listing 7) and the
+ * FWI gradient with wavefield checkpointing (Sec. 5.4, "gradient test").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  Grid.    `shape` is the PHYSICAL grid (points per axis).  The library adds
+ *           `nbl` damping-layer points on every side; the COMPUTATIONAL shape is
+ *           shape[a] + 2*nbl.  Axis order is (x, y, z) in 3D and (x, z) in 2D,
+ *           the last axis (depth) being contiguous in memory.  Fields exchanged
+ *           with the library are dense row-major float32 arrays in either the
+ *           physical or the computational shape, as each call states.
+ *  Units.   Spacing in metres, time in milliseconds, velocity in km/s (m/ms),
+ *           squared slowness m = 1/v^2 in ms^2/m^2.
+ *  Points.  Coordinates are double [npts][ndim] in metres relative to the
+ *           physical origin; every coordinate must lie in [0, (N_a-1) h_a].
+ *  Time.    u^{-1} = u^0 = 0.  Step n = 0..nt-2 makes u^{n+1} and adds the
+ *           source sample q^n into it, scaled by dt^2 / (m + eta dt/2).
+ *           Receivers record rec^n = P_r u^n for n = 0..nt-1.  Time series are
+ *           float32 [nt][npts] (row n holds sample n of every point).
+ *  Memory.  Array arguments may be HOST or DEVICE pointers (the library asks
+ *           the CUDA runtime which); host arrays are staged through
+ *           library-owned device buffers.  The caller owns every array it
+ *           passes; the library keeps no pointer past the call except where
+ *           stated.  Device arrays must live on the context's device.
+ *  Streams. `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *           Work is queued in stream order and the calls do not synchronise,
+ *           except that a host output array in pageable memory is complete
+ *           when the call returns.  Calls on one context must be ordered
+ *           (one stream, or synchronised by the caller).  Errors raised by
+ *           queued GPU work (a bounded wait that timed out) are reported by
+ *           fdw_sync and by the next call on the context.
+ *  Errors.  Every call returns fdw_status; FDW_OK = 0.  fdw_last_error gives
+ *           a message for the last failure on a context.
+ */
+#ifndef FDWAVE_H
+#define FDWAVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fdw_ctx fdw_ctx;      /* one shot: grid, model, wavefields, points, checkpoints */
+typedef struct fdw_batch fdw_batch;  /* several contexts stepped together in one launch per step */
+
+typedef enum {
+  FDW_OK = 0,
+  FDW_ERR_ARG = 1,            /* null / inconsistent argument */
+  FDW_ERR_SHAPE = 2,          /* ndim not 2 or 3, a dimension < 2, or too large */
+  FDW_ERR_ORDER = 3,          /* space order odd, < 2 or > 16 */
+  FDW_ERR_CFL = 4,            /* dt above the stability limit for vmax */
+  FDW_ERR_OUT_OF_DOMAIN = 5,  /* a point outside the physical domain */
+  FDW_ERR_OOM = 6,            /* device allocation failed */
+  FDW_ERR_CUDA = 7,           /* CUDA runtime error, or no usable GPU */
+  FDW_ERR_TIMEOUT = 8,        /* a device-side bounded wait gave up */
+  FDW_ERR_STATE = 9           /* call out of order (e.g. model not set) */
+} fdw_status;
+
+/* Storage types for the model and the checkpoint snapshots. */
+enum { FDW_F32 = 0, FDW_F16 = 1, FDW_BF16 = 2 };
+/* Layout of a field exchanged with the library. */
+enum { FDW_LAYOUT_PHYSICAL = 0, FDW_LAYOUT_COMPUTATIONAL = 1 };
+
+/* ---------------------------------------------------------------- host helpers */
+
+/* Library version as 10000*major + 100*minor + patch. */
+int fdw_version(void);
+
+/* Text of a status code (static string). */
+const char* fdw_status_string(fdw_status st);
+
+/* Central second-derivative weights c_0..c_r (r = p/2, c must hold r+1
+ * doubles) of order p, unscaled (multiply by 1/h^2).  Sec. 3.1: the order of
+ * the `dx2` expansion is a parameter; for p = 2 the paper prints [1, -2, 1].
+ * FDW_ERR_ORDER for an invalid p, FDW_ERR_ARG for c == NULL.  Host only. */
+fdw_status fdw_fd_weights(int space_order, double* c);
+
+/* Stability limit of the explicit scheme (von Neumann, undamped):
+ * dt_max = 2 / (vmax sqrt(sum_a S / h_a^2)) with S the largest |symbol| of the
+ * 1-D stencil.  Returns a negative value for invalid arguments.  Host only. */
+double fdw_dt_max(int ndim, const double* spacing, int space_order, double vmax);
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` for one problem:
+ *   ndim          2 or 3
+ *   shape         physical points per axis [ndim], each >= 2
+ *   spacing       grid spacing per axis [ndim], metres, > 0
+ *   space_order   even, 2..16
+ *   nbl           damping-layer points per side, >= 0
+ *   dt, nt        time step (ms) and number of time samples (>= 1)
+ *   vmax          largest velocity of any model that will be set (km/s); it
+ *                 sets the damping strength (Sec. 5, Eq. 3: eta is the
+ *                 spatially varying damping of the absorbing layer) and the
+ *                 stability check: dt > fdw_dt_max(...) gives FDW_ERR_CFL.
+ * Allocates the two wavefield buffers and the model buffer.  *out receives the
+ * context, or NULL on failure.  The damping is the built-in quadratic profile
+ * eta = sum_a 3 ln(1000) / (2 nbl h_a vmax) (d_a / nbl)^2 (d_a: cells into the
+ * layer along axis a) until fdw_set_damping replaces it. */
+fdw_status fdw_create(fdw_ctx** out, int ndim, const int64_t* shape, const double* spacing,
+                      int space_order, int nbl, double dt, int nt, double vmax, int device);
+
+/* Free a context and everything it owns (NULL is ignored).  Synchronises the
+ * device first. */
+void fdw_destroy(fdw_ctx* ctx);
+
+/* Message of the last failure on this context ("" when none). */
+const char* fdw_last_error(const fdw_ctx* ctx);
+
+/* Set the squared slowness m (float32, host or device).  layout
+ * FDW_LAYOUT_PHYSICAL: m has the physical shape and is extended into the layer
+ * by repeating the edge values; FDW_LAYOUT_COMPUTATIONAL: m has the
+ * computational shape.  m_dtype selects the STORAGE type on the device
+ * (FDW_F32, FDW_F16 or FDW_BF16); arithmetic stays float32.  m must be > 0. */
+fdw_status fdw_set_model(fdw_ctx* ctx, const float* m, int layout, int m_dtype, void* stream);
+
+/* Replace the built-in damping by a user field eta (float32, computational
+ * shape, >= 0, host or device), or restore the built-in profile with
+ * eta == NULL.  A field costs one more read per point and step. */
+fdw_status fdw_set_damping(fdw_ctx* ctx, const float* eta, void* stream);
+
+/* Source and receiver positions (Sec. 5.2: sparse points with their own
+ * coordinates).  xyz is double [n][ndim] (host), n >= 0.  The multilinear
+ * weights and the per-tile lists are built on the host and kept by the
+ * context.  FDW_ERR_OUT_OF_DOMAIN if a point lies outside the physical grid. */
+fdw_status fdw_set_sources(fdw_ctx* ctx, int nsrc, const double* xyz);
+fdw_status fdw_set_receivers(fdw_ctx* ctx, int nrec, const double* xyz);
+
+/* --------------------------------------------------------------- propagation */
+
+/* Forward modelling (Sec. 5.1, Listing 6, with the injection and sampling of
+ * Sec. 5.2): q [nt][nsrc] in, receiver traces rec [nt][nrec] out. */
+fdw_status fdw_forward(fdw_ctx* ctx, const float* q, float* rec, void* stream);
+
+/* Forward modelling that also keeps checkpoints for fdw_gradient: the pair
+ * (u^{jk}, u^{jk-1}) every k = ckpt_every steps, stored as snap_dtype
+ * (FDW_F32, FDW_F16 or FDW_BF16; 16-bit snapshots carry one float32 scale per
+ * snapshot), plus a copy of q.  The checkpoints live on the device until the
+ * next checkpointed forward or fdw_destroy. */
+fdw_status fdw_forward_ckpt(fdw_ctx* ctx, const float* q, float* rec, int ckpt_every,
+                            int snap_dtype, void* stream);
+
+/* Adjoint modelling (Sec. 5.1, Listing 7): the receivers inject d [nt][nrec]
+ * backward in time and the sources sample qadj [nt][nsrc] (out), so that
+ * <F q, d> = <q, F^T d> (Sec. 5.3, Eq. 4).  qadj^n = P_s lambda^{n+1}. */
+fdw_status fdw_adjoint(fdw_ctx* ctx, const float* d, float* qadj, void* stream);
+
+/* FWI gradient (Sec. 5.4) with respect to m of sum_n <r^n, P_r u^n>, where
+ * r = resid - resid_sub ([nt][nrec] each; resid_sub may be NULL) and u is the
+ * wavefield of the last fdw_forward_ckpt.  For the misfit
+ * J = 1/2 sum |rec - d_obs|^2 pass resid = rec, resid_sub = d_obs.
+ * grad (out, float32) has the computational shape (grad_layout
+ * FDW_LAYOUT_COMPUTATIONAL), or the physical shape with the layer cells summed
+ * onto the edge cells they repeat (FDW_LAYOUT_PHYSICAL, the gradient with
+ * respect to a physical model set with FDW_LAYOUT_PHYSICAL).
+ * FDW_ERR_STATE without a preceding checkpointed forward. */
+fdw_status fdw_gradient(fdw_ctx* ctx, const float* resid, const float* resid_sub, float* grad,
+                        int grad_layout, void* stream);
+
+/* Copy the newest wavefield u^{nt-1} of the last forward call (or lambda^1 of
+ * the last adjoint when which == 1) to out (float32, computational shape). */
+fdw_status fdw_get_wavefield(fdw_ctx* ctx, int which, float* out, void* stream);
+
+/* Wait for the context's queued work and report device-side errors. */
+fdw_status fdw_sync(fdw_ctx* ctx);
+
+/* ------------------------------------------------------------------ tuning */
+
+/* Brute-force search over tile shapes, x-chunk lengths and pipeline depths
+ * (Sec. 3.3.3: block sizes found by a brute-force search), timing `steps`
+ * forward steps each on the current model.  The choice is kept by the
+ * context and, when the environment variable FDW_AUTOTUNE_CACHE names a file,
+ * cached there per (GPU, order, shape, model type).  Synchronises. */
+fdw_status fdw_autotune(fdw_ctx* ctx, int steps);
+
+/* Force a tile configuration: tile index (0..3, -1 = default), x-chunk length
+ * (0 = default) and pipeline stages (0 = default). */
+fdw_status fdw_set_tiling(fdw_ctx* ctx, int tile, int xchunk, int stages);
+
+/* Tile configuration in use: out[0] = tile index, out[1] = x-chunk length,
+ * out[2] = pipeline stages, out[3] = CTAs per launch, out[4] = work units. */
+fdw_status fdw_get_tiling(fdw_ctx* ctx, int* out5);
+
+/* -------------------------------------------------------------- batched shots */
+
+/* Group contexts that share order, spacing, dt, nt and model storage type so
+ * that every time step of all of them runs as one launch over one table of
+ * work units (grids may differ in size).  The contexts must outlive the
+ * batch.  The batch keeps its own tiling (fdw_batch_autotune). */
+fdw_status fdw_batch_create(fdw_batch** out, int nshots, fdw_ctx* const* ctxs);
+void fdw_batch_destroy(fdw_batch* b);
+const char* fdw_batch_last_error(const fdw_batch* b);
+
+/* Forward modelling of every shot: q[s] and rec[s] as in fdw_forward. */
+fdw_status fdw_batch_forward(fdw_batch* b, const float* const* q, float* const* rec,
+                             void* stream);
+
+/* Checkpointed forward and gradient of every shot, as fdw_forward_ckpt and
+ * fdw_gradient per shot (resid_sub may be NULL, or hold NULL entries). */
+fdw_status fdw_batch_forward_ckpt(fdw_batch* b, const float* const* q, float* const* rec,
+                                  int ckpt_every, int snap_dtype, void* stream);
+fdw_status fdw_batch_gradient(fdw_batch* b, const float* const* resid,
+                              const float* const* resid_sub, float* const* grad,
+                              int grad_layout, void* stream);
+
+fdw_status fdw_batch_autotune(fdw_batch* b, int steps);
+fdw_status fdw_batch_get_tiling(fdw_batch* b, int* out5);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDWAVE_H */

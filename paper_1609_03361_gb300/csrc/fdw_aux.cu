@@ -1,0 +1,267 @@
+// Auxiliary kernels of libfdwave: per-call work around the time loop.
+//  - sampling of the last time level (grid-to-point, Sec. 5.2),
+//  - model set-up (edge extension into the layer, storage-type conversion),
+//  - damping-field set-up,
+//  - checkpoint snapshots: absolute maximum, pack to 16 bits with a scale,
+//    unpack,
+//  - gradient output (scaling and folding of the layer onto the edges),
+//  - copy of a pitched field to a dense array.
+// All index arithmetic is 64-bit; grid-stride loops cover any size.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "fdw_internal.h"
+
+namespace fdw {
+namespace {
+
+constexpr int kThreads = 256;
+
+__host__ __device__ inline long long dense_points(const Geom& g) {
+  return (long long)g.nx * g.ny * g.nz;
+}
+
+__device__ inline long long pitched(const Geom& g, long long i) {
+  // dense index (x, y, z) -> pitched offset
+  const long long z = i % g.nz;
+  const long long xy = i / g.nz;
+  return xy * g.nzp + z;
+}
+
+inline int blocks_for(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  if (b > 152LL * 32) b = 152LL * 32;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+__global__ void sample_kernel(const ShotDesc* shots, int slot, int row) {
+  const ShotDesc& d = shots[blockIdx.y];
+  const float* u = d.u + (long long)slot * d.uslot;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.smp_n; j += gridDim.x * blockDim.x) {
+    const int bx = d.pt_base[3 * j], by = d.pt_base[3 * j + 1], bz = d.pt_base[3 * j + 2];
+    const float* w = d.pt_w + 8 * j;
+    float acc = 0.f;
+    for (int c = 0; c < 8; ++c) {
+      const float wc = w[c];
+      if (wc != 0.f) {
+        const long long off =
+            ((long long)(bx + ((c >> 2) & 1)) * d.ny + (by + ((c >> 1) & 1))) * d.nzp + bz + (c & 1);
+        acc = fmaf(wc, u[off], acc);
+      }
+    }
+    d.smp_out[(long long)row * d.smp_ld + j] = acc;
+  }
+}
+
+__global__ void model_kernel(const float* in, int layout, int px, int py, int pz, int nbl,
+                             int ndim, void* out, int mtype, Geom g) {
+  const long long n = dense_points(g);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long z = i % g.nz;
+    const long long y = (i / g.nz) % g.ny;
+    const long long x = i / ((long long)g.nz * g.ny);
+    float v;
+    if (layout == 0) {  // physical: clamp each computational index into the physical range
+      long long cx = x - nbl, cy = (ndim == 3) ? y - nbl : 0, cz = z - nbl;
+      cx = cx < 0 ? 0 : (cx > px - 1 ? px - 1 : cx);
+      cy = cy < 0 ? 0 : (cy > py - 1 ? py - 1 : cy);
+      cz = cz < 0 ? 0 : (cz > pz - 1 ? pz - 1 : cz);
+      v = in[(cx * py + cy) * pz + cz];
+    } else {
+      v = in[i];
+    }
+    const long long o = pitched(g, i);
+    if (mtype == kF16) static_cast<__half*>(out)[o] = __float2half_rn(v);
+    else if (mtype == kBF16) static_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(v);
+    else static_cast<float*>(out)[o] = v;
+  }
+}
+
+__global__ void eta_field_kernel(const float* in, float scale, float* out, Geom g) {
+  const long long n = dense_points(g);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[pitched(g, i)] = in[i] * scale;
+}
+
+// max(|a|, |b|) over a pair of pitched fields, per shot (blockIdx.y).
+__global__ void absmax_kernel(const AuxShot* shots) {
+  const AuxShot& s = shots[blockIdx.y];
+  const long long n = dense_points(s.g);
+  float m = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long o = pitched(s.g, i);
+    m = fmaxf(m, fmaxf(fabsf(s.a[o]), fabsf(s.b[o])));
+  }
+  for (int k = 16; k > 0; k >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, k));
+  __shared__ float red[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    atomicMax(s.amax, __float_as_uint(m));  // non-negative floats order like their bits
+  }
+}
+
+// Scale that maps the pair's maximum to 2^14 (16-bit storage), 1 otherwise.
+__device__ inline float snap_scale(const unsigned int* amax, int stype) {
+  if (stype == kF32) return 1.f;
+  const float m = __uint_as_float(*amax);
+  return m > 0.f ? 16384.f / m : 1.f;
+}
+
+__global__ void pack_kernel(const AuxShot* shots, int stype) {
+  const AuxShot& s = shots[blockIdx.y];
+  const long long n = dense_points(s.g);
+  const float sc = snap_scale(s.amax, stype);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long o = pitched(s.g, i);
+    const float a = s.a[o], b = s.b[o];
+    if (stype == kF16) {
+      __half* h = static_cast<__half*>(s.snap);
+      h[i] = __float2half_rn(a * sc);
+      h[n + i] = __float2half_rn(b * sc);
+    } else if (stype == kBF16) {
+      __nv_bfloat16* h = static_cast<__nv_bfloat16*>(s.snap);
+      h[i] = __float2bfloat16_rn(a * sc);
+      h[n + i] = __float2bfloat16_rn(b * sc);
+    } else {
+      float* h = static_cast<float*>(s.snap);
+      h[i] = a;
+      h[n + i] = b;
+    }
+  }
+}
+
+__global__ void unpack_kernel(const AuxShot* shots, int stype) {
+  const AuxShot& s = shots[blockIdx.y];
+  const long long n = dense_points(s.g);
+  const float inv = 1.f / snap_scale(s.amax, stype);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long o = pitched(s.g, i);
+    float a, b;
+    if (stype == kF16) {
+      const __half* h = static_cast<const __half*>(s.snap);
+      a = __half2float(h[i]) * inv;
+      b = __half2float(h[n + i]) * inv;
+    } else if (stype == kBF16) {
+      const __nv_bfloat16* h = static_cast<const __nv_bfloat16*>(s.snap);
+      a = __bfloat162float(h[i]) * inv;
+      b = __bfloat162float(h[n + i]) * inv;
+    } else {
+      const float* h = static_cast<const float*>(s.snap);
+      a = h[i];
+      b = h[n + i];
+    }
+    s.a[o] = a;
+    s.b[o] = b;
+  }
+}
+
+// Gradient output.  layout 1: computational shape, out = scale * acc.
+// layout 0: physical shape, each physical cell sums the computational cells
+// whose clamped index is that cell (the adjoint of the edge extension).
+__global__ void grad_out_kernel(const float* acc, Geom g, float scale, float* out, int layout,
+                                int nbl, int ndim, int px, int py, int pz) {
+  if (layout == 1) {
+    const long long n = dense_points(g);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+      out[i] = scale * acc[pitched(g, i)];
+    return;
+  }
+  const long long n = (long long)px * py * pz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i % pz);
+    const int j = (int)((i / pz) % py);
+    const int l = (int)(i / ((long long)pz * py));
+    // computational ranges mapping onto (l, j, k)
+    int xl = l + nbl, xh = l + nbl;
+    if (l == 0) xl = 0;
+    if (l == px - 1) xh = px - 1 + 2 * nbl;
+    int yl = 0, yh = 0;
+    if (ndim == 3) {
+      yl = j + nbl; yh = j + nbl;
+      if (j == 0) yl = 0;
+      if (j == py - 1) yh = py - 1 + 2 * nbl;
+    }
+    int zl = k + nbl, zh = k + nbl;
+    if (k == 0) zl = 0;
+    if (k == pz - 1) zh = pz - 1 + 2 * nbl;
+    double s = 0.0;
+    for (int x = xl; x <= xh; ++x)
+      for (int y = yl; y <= yh; ++y)
+        for (int z = zl; z <= zh; ++z) s += acc[((long long)x * g.ny + y) * g.nzp + z];
+    out[i] = (float)(scale * s);
+  }
+}
+
+__global__ void copy_out_kernel(const float* f, Geom g, float* out) {
+  const long long n = dense_points(g);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = f[pitched(g, i)];
+}
+
+}  // namespace
+
+cudaError_t launch_sample(const ShotDesc* shots, int nshots, int maxpts, int slot, int row,
+                          cudaStream_t s) {
+  if (maxpts <= 0 || nshots <= 0) return cudaSuccess;
+  dim3 grid((maxpts + kThreads - 1) / kThreads, nshots);
+  sample_kernel<<<grid, kThreads, 0, s>>>(shots, slot, row);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_model(const float* in, int layout, int px, int py, int pz, int nbl, int ndim,
+                         void* out, int mtype, Geom g, cudaStream_t s) {
+  model_kernel<<<blocks_for(dense_points(g)), kThreads, 0, s>>>(in, layout, px, py, pz, nbl, ndim,
+                                                                out, mtype, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eta_field(const float* in, float scale, float* out, Geom g, cudaStream_t s) {
+  eta_field_kernel<<<blocks_for(dense_points(g)), kThreads, 0, s>>>(in, scale, out, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_absmax(const AuxShot* shots, int nshots, long long maxpts, cudaStream_t s) {
+  dim3 grid(blocks_for(maxpts), nshots);
+  absmax_kernel<<<grid, kThreads, 0, s>>>(shots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const AuxShot* shots, int nshots, long long maxpts, int stype,
+                        cudaStream_t s) {
+  dim3 grid(blocks_for(maxpts), nshots);
+  pack_kernel<<<grid, kThreads, 0, s>>>(shots, stype);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const AuxShot* shots, int nshots, long long maxpts, int stype,
+                          cudaStream_t s) {
+  dim3 grid(blocks_for(maxpts), nshots);
+  unpack_kernel<<<grid, kThreads, 0, s>>>(shots, stype);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_out(const float* acc, Geom g, float scale, float* out, int layout,
+                            int nbl, int ndim, int px, int py, int pz, cudaStream_t s) {
+  const long long n = layout == 1 ? dense_points(g) : (long long)px * py * pz;
+  grad_out_kernel<<<blocks_for(n), kThreads, 0, s>>>(acc, g, scale, out, layout, nbl, ndim, px,
+                                                      py, pz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_out(const float* field, Geom g, float* out, cudaStream_t s) {
+  copy_out_kernel<<<blocks_for(dense_points(g)), kThreads, 0, s>>>(field, g, out);
+  return cudaGetLastError();
+}
+
+}  // namespace fdw

@@ -1,0 +1,58 @@
+// Internal declarations of libfdwave shared by the runtime and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fdw_types.h"
+
+namespace fdw {
+
+// Tile shapes of the step kernel: NY points along y per consumer thread and BY
+// consumer warps, so a tile is (BY * NY) x 32 points in (y, z).
+struct TileShape {
+  int ny_pts;
+  int warps;
+};
+constexpr int kNumTiles = 4;
+constexpr TileShape kTiles[kNumTiles] = {{2, 8}, {4, 8}, {2, 4}, {1, 1}};
+
+// Kernel registry: one translation unit per stencil radius.
+const void* step_kernel_r1(int tile, bool grad);
+const void* step_kernel_r2(int tile, bool grad);
+const void* step_kernel_r3(int tile, bool grad);
+const void* step_kernel_r4(int tile, bool grad);
+const void* step_kernel_r5(int tile, bool grad);
+const void* step_kernel_r6(int tile, bool grad);
+const void* step_kernel_r7(int tile, bool grad);
+const void* step_kernel_r8(int tile, bool grad);
+
+// Geometry of one pitched field for the auxiliary kernels.
+struct Geom {
+  int nx, ny, nz, nzp;
+};
+
+// Per-shot descriptor of the auxiliary (per-call, not per-step) kernels.
+struct AuxShot {
+  Geom g;
+  float* a;             // first field (slot base)
+  float* b;             // second field
+  void* snap;           // snapshot pair base (two compact fields)
+  unsigned int* amax;   // absolute maximum of the pair, float bits
+};
+
+cudaError_t launch_sample(const ShotDesc* shots, int nshots, int maxpts, int slot, int row,
+                          cudaStream_t s);
+cudaError_t launch_model(const float* in, int layout, int phys_x, int phys_y, int phys_z,
+                         int nbl, int ndim, void* out, int mtype, Geom g, cudaStream_t s);
+cudaError_t launch_eta_field(const float* in, float scale, float* out, Geom g, cudaStream_t s);
+cudaError_t launch_absmax(const AuxShot* shots, int nshots, long long maxpts, cudaStream_t s);
+cudaError_t launch_pack(const AuxShot* shots, int nshots, long long maxpts, int stype,
+                        cudaStream_t s);
+cudaError_t launch_unpack(const AuxShot* shots, int nshots, long long maxpts, int stype,
+                          cudaStream_t s);
+cudaError_t launch_grad_out(const float* acc, Geom g, float scale, float* out, int layout,
+                            int nbl, int ndim, int phys_x, int phys_y, int phys_z,
+                            cudaStream_t s);
+cudaError_t launch_copy_out(const float* field, Geom g, float* out, cudaStream_t s);
+
+}  // namespace fdw

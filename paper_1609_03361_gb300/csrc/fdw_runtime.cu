@@ -1,0 +1,1606 @@
+// Host runtime and C ABI of libfdwave.
+//
+// A context (fdw_ctx) owns one shot: its grid, model, damping, wavefield
+// buffers, sparse points and checkpoint store.  A plan (Plan) turns one or more
+// contexts into what the time-step kernel walks: a table of work units (one
+// column tile of a shot streamed along an x chunk), per-unit injection and
+// sampling lists for each role (forward, adjoint, recompute) and per-shot
+// descriptors with TMA tensor maps.  Time loops are captured once into CUDA
+// graphs and replayed.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <memory>
+#include <sstream>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "fdw_internal.h"
+#include "fdwave.h"
+
+namespace fdw {
+
+// ---------------------------------------------------------------- errors
+
+struct Error {
+  fdw_status st;
+  std::string msg;
+};
+
+[[noreturn]] static void fail(fdw_status st, const std::string& msg) { throw Error{st, msg}; }
+
+static void cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation) fail(FDW_ERR_OOM, std::string(what) + ": out of device memory");
+  fail(FDW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(call) cuda_check((call), #call)
+
+template <class T>
+static T* dalloc(size_t count) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  cuda_check(cudaMalloc(&p, count * sizeof(T)), "cudaMalloc");
+  return static_cast<T*>(p);
+}
+
+static void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+// ---------------------------------------------------------------- host math
+
+// Second-derivative weights at offsets 0..r of the 2r+1 point central stencil,
+// by Fornberg's recursion (Math. Comp. 51, 1988) on the nodes 0, 1, -1, 2, -2, ...
+static std::vector<double> fornberg_second_derivative(int p) {
+  const int r = p / 2;
+  const int N = 2 * r + 1;
+  std::vector<double> x(N);
+  x[0] = 0.0;
+  for (int j = 1; j <= r; ++j) {
+    x[2 * j - 1] = j;
+    x[2 * j] = -j;
+  }
+  const int M = 2;
+  // d[m][n][v] flattened
+  std::vector<double> d((M + 1) * N * N, 0.0);
+  auto D = [&](int m, int n, int v) -> double& { return d[(m * N + n) * N + v]; };
+  D(0, 0, 0) = 1.0;
+  double c1 = 1.0;
+  for (int n = 1; n < N; ++n) {
+    double c2 = 1.0;
+    for (int v = 0; v < n; ++v) {
+      const double c3 = x[n] - x[v];
+      c2 *= c3;
+      for (int m = 0; m <= std::min(n, M); ++m) {
+        const double lower = m ? D(m - 1, n - 1, v) : 0.0;
+        D(m, n, v) = (x[n] * D(m, n - 1, v) - m * lower) / c3;
+      }
+    }
+    for (int m = 0; m <= std::min(n, M); ++m) {
+      const double lower = m ? D(m - 1, n - 1, n - 1) : 0.0;
+      D(m, n, n) = c1 / c2 * (m * lower - x[n - 1] * D(m, n - 1, n - 1));
+    }
+    c1 = c2;
+  }
+  std::vector<double> c(r + 1);
+  c[0] = D(M, N - 1, 0);
+  for (int j = 1; j <= r; ++j) c[j] = 0.5 * (D(M, N - 1, 2 * j - 1) + D(M, N - 1, 2 * j));
+  return c;
+}
+
+static bool valid_order(int p) { return p >= 2 && p <= 16 && p % 2 == 0; }
+
+static double symbol_max(int p) {
+  const std::vector<double> c = fornberg_second_derivative(p);
+  double s = c[0];
+  for (int j = 1; j <= p / 2; ++j) s += 2.0 * ((j % 2) ? -1.0 : 1.0) * c[j];
+  return std::fabs(s);
+}
+
+static double dt_limit(int ndim, const double* h, int p, double vmax) {
+  const double S = symbol_max(p);
+  double acc = 0.0;
+  for (int a = 0; a < ndim; ++a) acc += S / (h[a] * h[a]);
+  return 2.0 / (vmax * std::sqrt(acc));
+}
+
+// ---------------------------------------------------------------- TMA maps
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) fail(FDW_ERR_CUDA, "cuTensorMapEncodeTiled not found");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Pitched field(s) [slots][nx][ny][nzp] of element type dt; rank 3 when slots == 0.
+static void make_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void* base,
+                     int nx, int ny, int nz, int nzp, int slots, long long slot_elems, int box_z,
+                     int box_y) {
+  cuuint64_t dims[4] = {(cuuint64_t)nz, (cuuint64_t)ny, (cuuint64_t)nx, (cuuint64_t)(slots ? slots : 1)};
+  cuuint64_t strides[3] = {(cuuint64_t)nzp * esize, (cuuint64_t)nzp * ny * esize,
+                           (cuuint64_t)slot_elems * esize};
+  cuuint32_t box[4] = {(cuuint32_t)box_z, (cuuint32_t)box_y, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  const cuuint32_t rank = slots ? 4 : 3;
+  CUresult r = encode_fn()(map, dt, rank, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    std::ostringstream os;
+    os << "cuTensorMapEncodeTiled failed (" << (int)r << ") dims " << nz << "x" << ny << "x" << nx
+       << " box " << box_z << "x" << box_y;
+    fail(FDW_ERR_CUDA, os.str());
+  }
+}
+
+// ---------------------------------------------------------------- kernels
+
+static const void* step_fn(int r, int tile, bool grad) {
+  switch (r) {
+    case 1: return step_kernel_r1(tile, grad);
+    case 2: return step_kernel_r2(tile, grad);
+    case 3: return step_kernel_r3(tile, grad);
+    case 4: return step_kernel_r4(tile, grad);
+    case 5: return step_kernel_r5(tile, grad);
+    case 6: return step_kernel_r6(tile, grad);
+    case 7: return step_kernel_r7(tile, grad);
+    case 8: return step_kernel_r8(tile, grad);
+  }
+  return nullptr;
+}
+
+static int device_sms(int dev) {
+  int v = 0;
+  CK(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+  return v;
+}
+
+static int device_smem_optin(int dev) {
+  int v = 0;
+  CK(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  return v;
+}
+
+static bool env_flag(const char* name) {
+  const char* v = std::getenv(name);
+  return v && *v && std::strcmp(v, "0") != 0;
+}
+
+}  // namespace fdw
+
+using namespace fdw;
+
+// ---------------------------------------------------------------- points
+
+struct PointSet {
+  int n = 0;
+  std::vector<double> xyz;   // [n][ndim]
+  std::vector<int> base;     // [n][3] computational base node (internal x, y, z)
+  std::vector<float> w;      // [n][8]
+  int* d_base = nullptr;
+  float* d_w = nullptr;
+  void release() {
+    dfree(d_base);
+    dfree(d_w);
+    d_base = nullptr;
+    d_w = nullptr;
+  }
+};
+
+struct Plan;
+
+struct fdw_ctx {
+  int device = 0;
+  int ndim = 3;
+  int64_t phys[3] = {1, 1, 1};  // internal (x, y, z); y = 1 in 2D
+  int nx = 1, ny = 1, nz = 1, nzp = 32;
+  double h[3] = {1, 1, 1};      // internal (x, y, z)
+  int order = 2, r = 1, nbl = 0;
+  double dt = 1.0;
+  int nt = 1;
+  double vmax = 1.0;
+  long long slot = 0;           // floats per pitched field
+
+  float* u = nullptr;           // 2 slots
+  void* m = nullptr;
+  int mtype = kF32;
+  bool model_set = false;
+  float* eta = nullptr;         // eta*dt/2 profiles [nx + ny + nz]
+  float* etaf = nullptr;        // eta*dt/2 field (pitched)
+  bool use_etaf = false;
+  PointSet src, rec;
+  int points_version = 0;
+
+  // checkpoint store
+  int ckpt_k = 0, snap_type = -1, nsnap = 0;
+  void* snaps = nullptr;
+  unsigned int* amax = nullptr;
+  float* seg = nullptr;         // k+1 slots
+  int seg_slots = 0;
+  float* lam = nullptr;         // 2 slots
+  float* acc = nullptr;         // 1 slot
+  float* qsave = nullptr;
+  bool have_ckpt = false;
+  bool fwd_done = false, adj_done = false;
+  int buffers_version = 0;
+
+  // tiling override
+  int tile = -1, xchunk = 0, stages = 0;
+
+  // staging buffers for host arrays
+  std::map<int, std::pair<void*, size_t>> staging;
+
+  std::unique_ptr<Plan> plan;
+  std::string err;
+  ~fdw_ctx();
+};
+
+enum Role { kRoleFwd = 0, kRoleAdj = 1, kRoleRec = 2, kNumRoles = 3 };
+
+struct RoleLists {
+  std::vector<int> inj_ptr, smp_ptr, smp_pts;
+  std::vector<InjNode> nodes;
+  std::vector<InjTerm> terms;
+  int* d_inj_ptr = nullptr;
+  int* d_smp_ptr = nullptr;
+  int* d_smp_pts = nullptr;
+  InjNode* d_nodes = nullptr;
+  InjTerm* d_terms = nullptr;
+  void release() {
+    dfree(d_inj_ptr); dfree(d_smp_ptr); dfree(d_smp_pts); dfree(d_nodes); dfree(d_terms);
+    d_inj_ptr = d_smp_ptr = d_smp_pts = nullptr;
+    d_nodes = nullptr;
+    d_terms = nullptr;
+  }
+};
+
+struct Plan {
+  std::vector<fdw_ctx*> shots;
+  int device = 0;
+  int r = 1;
+  int tile = 0, lx = 16, stages = 8;
+  int tile_req = -1, lx_req = 0, stages_req = 0;
+  std::vector<Unit> units;
+  Unit* d_units = nullptr;
+  RoleLists lists[kNumRoles];
+  std::vector<ShotDesc> hdesc[kNumRoles];
+  ShotDesc* d_desc[kNumRoles] = {nullptr, nullptr, nullptr};
+  int* d_err = nullptr;
+  cudaStream_t cap = nullptr;
+  std::map<std::string, cudaGraphExec_t> graphs;
+  // aux descriptors for snapshots: [nsnap][nshots] pack and unpack
+  AuxShot* d_pack = nullptr;
+  AuxShot* d_unpack = nullptr;
+  int aux_version = -1;
+  std::vector<int> built_versions;   // points/buffers versions the lists and maps were built for
+  struct LaunchInfo {
+    const void* fn;
+    int grid, threads;
+    size_t smem;
+    int stage_bytes, off_p, off_m, off_f, off_e;
+  };
+  std::map<std::tuple<int, int, int, int, int, int>, LaunchInfo> launch_cache;
+  std::vector<double> weights;       // unscaled second-derivative weights c_0..c_r
+  bool built = false;
+  int max_rec = 0, max_src = 0;
+  long long max_points = 0;
+
+  void clear_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
+  void release_lists() {
+    for (auto& l : lists) l.release();
+    dfree(d_units);
+    d_units = nullptr;
+  }
+  ~Plan() {
+    clear_graphs();
+    release_lists();
+    for (auto& d : d_desc) dfree(d);
+    dfree(d_err);
+    dfree(d_pack);
+    dfree(d_unpack);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+fdw_ctx::~fdw_ctx() {
+  plan.reset();
+  dfree(u); dfree(m); dfree(eta); dfree(etaf);
+  src.release(); rec.release();
+  dfree(snaps); dfree(amax); dfree(seg); dfree(lam); dfree(acc); dfree(qsave);
+  for (auto& kv : staging) dfree(kv.second.first);
+}
+
+struct fdw_batch {
+  std::vector<fdw_ctx*> shots;
+  std::unique_ptr<Plan> plan;
+  std::string err;
+};
+
+// ---------------------------------------------------------------- helpers
+
+static int msize(int t) { return t == kF32 ? 4 : 2; }
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static void* staging_buf(fdw_ctx* c, int key, size_t bytes) {
+  auto it = c->staging.find(key);
+  if (it != c->staging.end() && it->second.second >= bytes) return it->second.first;
+  if (it != c->staging.end()) dfree(it->second.first);
+  void* p = dalloc<unsigned char>(bytes);
+  c->staging[key] = {p, bytes};
+  return p;
+}
+
+// Device view of a caller input array (copied when it lives on the host).
+static const float* device_in(fdw_ctx* c, int key, const float* p, size_t count, cudaStream_t s) {
+  if (!p || count == 0) return p;
+  if (is_device_ptr(p)) return p;
+  float* d = static_cast<float*>(staging_buf(c, key, count * sizeof(float)));
+  CK(cudaMemcpyAsync(d, p, count * sizeof(float), cudaMemcpyHostToDevice, s));
+  return d;
+}
+
+// Device buffer for a caller output array; copy_back() is needed when host.
+static float* device_out(fdw_ctx* c, int key, float* p, size_t count, bool* host) {
+  *host = false;
+  if (!p || count == 0) return p;
+  if (is_device_ptr(p)) return p;
+  *host = true;
+  return static_cast<float*>(staging_buf(c, key, count * sizeof(float)));
+}
+
+static void set_device(int dev) { CK(cudaSetDevice(dev)); }
+
+// ---------------------------------------------------------------- points
+
+static void compute_points(fdw_ctx* c, PointSet& ps, int n, const double* xyz) {
+  if (n < 0 || (n > 0 && !xyz)) fail(FDW_ERR_ARG, "bad point array");
+  PointSet out;
+  out.n = n;
+  out.xyz.assign(xyz, xyz + (size_t)n * c->ndim);
+  out.base.resize((size_t)n * 3);
+  out.w.resize((size_t)n * 8);
+  // internal axes: 3D (x, y, z); 2D (x, -, z) with user axes (x, z)
+  for (int j = 0; j < n; ++j) {
+    int b[3] = {0, 0, 0};
+    double f[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+      if (c->ndim == 2 && a == 1) continue;
+      const int ua = (c->ndim == 2 && a == 2) ? 1 : a;
+      const double xv = xyz[(size_t)j * c->ndim + ua];
+      const double top = (double)(c->phys[a] - 1) * c->h[a];
+      if (!(xv >= 0.0) || !(xv <= top)) {
+        std::ostringstream os;
+        os << "point " << j << " coordinate " << ua << " = " << xv << " outside [0, " << top << "]";
+        fail(FDW_ERR_OUT_OF_DOMAIN, os.str());
+      }
+      const double xi = xv / c->h[a];
+      long long i = (long long)std::floor(xi);
+      if (i < 0) i = 0;
+      if (i > c->phys[a] - 2) i = c->phys[a] - 2;
+      b[a] = (int)i + c->nbl;
+      f[a] = xi - (double)i;
+    }
+    for (int a = 0; a < 3; ++a) out.base[(size_t)j * 3 + a] = (c->ndim == 2 && a == 1) ? 0 : b[a];
+    for (int cc = 0; cc < 8; ++cc) {
+      const int bx = (cc >> 2) & 1, by = (cc >> 1) & 1, bz = cc & 1;
+      double w = (bx ? f[0] : 1.0 - f[0]) * (bz ? f[2] : 1.0 - f[2]);
+      if (c->ndim == 3) w *= by ? f[1] : 1.0 - f[1];
+      else if (by) w = 0.0;
+      out.w[(size_t)j * 8 + cc] = (float)w;
+    }
+  }
+  if (n > 0) {
+    out.d_base = dalloc<int>((size_t)n * 3);
+    out.d_w = dalloc<float>((size_t)n * 8);
+    CK(cudaMemcpy(out.d_base, out.base.data(), sizeof(int) * n * 3, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(out.d_w, out.w.data(), sizeof(float) * n * 8, cudaMemcpyHostToDevice));
+  }
+  ps.release();
+  ps = std::move(out);
+  c->points_version++;
+}
+
+// ---------------------------------------------------------------- plan
+
+struct StageLayout {
+  int off_p, off_m, off_f, off_e, bytes;
+};
+
+static int round128(int x) { return (x + 127) & ~127; }
+
+static StageLayout stage_layout(int r, int tile, int mt_bytes, bool grad, bool etaf) {
+  const TileShape t = kTiles[tile];
+  const int TY = t.ny_pts * t.warps;
+  const int R4 = (r + 3) & ~3;
+  const int ZW = kTZ + 2 * R4, YW = TY + 2 * r;
+  StageLayout L;
+  int off = round128(YW * ZW * 4);
+  L.off_p = off;
+  off += round128(TY * kTZ * 4);
+  L.off_m = off;
+  off += round128(TY * kTZ * mt_bytes);
+  L.off_f = off;
+  if (grad) off += round128(TY * kTZ * 4);
+  L.off_e = off;
+  if (etaf) off += round128(TY * kTZ * 4);
+  L.bytes = off;
+  return L;
+}
+
+static size_t smem_bytes(const StageLayout& L, int stages) {
+  return (size_t)stages * L.bytes + (size_t)(2 * stages + 1) * 8 + 128;
+}
+
+static int plan_mtype(const Plan& pl) { return pl.shots[0]->mtype; }
+static bool plan_etaf(const Plan& pl) {
+  for (auto* c : pl.shots)
+    if (c->use_etaf) return true;
+  return false;
+}
+
+static void configure_kernel(const void* fn, size_t smem) {
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+}
+
+// Occupancy-limited number of resident CTAs of a launch.
+static int resident_ctas(const Plan& pl, int tile, int stages, bool grad) {
+  const StageLayout L = stage_layout(pl.r, tile, 4, grad, true);
+  const size_t smem = smem_bytes(L, stages);
+  const void* fn = step_fn(pl.r, tile, grad);
+  configure_kernel(fn, smem);
+  int nb = 0;
+  const int threads = (kTiles[tile].warps + 1) * 32;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem));
+  return std::max(nb, 1) * device_sms(pl.device);
+}
+
+static int max_stages(const Plan& pl, int tile) {
+  const StageLayout L = stage_layout(pl.r, tile, 4, true, true);
+  const int cap = device_smem_optin(pl.device) - 1024;  // static shared memory and slack
+  int s = 2 * pl.r + 8;
+  while (s > pl.r + 2 && (int)smem_bytes(L, s) > cap) --s;
+  return s;
+}
+
+static void choose_default_tiling(Plan& pl) {
+  bool all2d = true;
+  for (auto* c : pl.shots)
+    if (c->ny > 1) all2d = false;
+  pl.tile = pl.tile_req >= 0 ? pl.tile_req : (all2d ? 3 : 0);
+  const int ms = max_stages(pl, pl.tile);
+  pl.stages = pl.stages_req > 0 ? std::min(pl.stages_req, ms) : std::min(pl.r + 4, ms);
+  if (pl.stages < pl.r + 2) fail(FDW_ERR_ARG, "pipeline too shallow for this order");
+  if (pl.lx_req > 0) {
+    pl.lx = pl.lx_req;
+    return;
+  }
+  // aim at >= 4 units per resident CTA so the static schedule balances
+  const int slots = resident_ctas(pl, pl.tile, pl.stages, false);
+  const int TY = kTiles[pl.tile].ny_pts * kTiles[pl.tile].warps;
+  long long cols = 0;
+  int nxmax = 1;
+  for (auto* c : pl.shots) {
+    cols += (long long)((c->ny + TY - 1) / TY) * ((c->nz + kTZ - 1) / kTZ);
+    nxmax = std::max(nxmax, c->nx);
+  }
+  long long chunks = (4LL * slots + cols - 1) / std::max(cols, 1LL);
+  chunks = std::max(1LL, std::min<long long>(chunks, nxmax));
+  pl.lx = std::max(8, (int)((nxmax + chunks - 1) / chunks));
+}
+
+static void upload_vec(void** dptr, const void* src, size_t bytes) {
+  dfree(*dptr);
+  *dptr = dalloc<unsigned char>(bytes);
+  if (bytes) CK(cudaMemcpy(*dptr, src, bytes, cudaMemcpyHostToDevice));
+}
+
+// Units and the per-unit injection / sampling lists of each role.
+static void build_lists(Plan& pl) {
+  pl.release_lists();
+  pl.clear_graphs();
+  const TileShape t = kTiles[pl.tile];
+  const int TY = t.ny_pts * t.warps;
+  pl.units.clear();
+  std::vector<int> shot_first(pl.shots.size() + 1, 0);
+  std::vector<std::array<int, 3>> counts(pl.shots.size());
+  for (size_t s = 0; s < pl.shots.size(); ++s) {
+    const fdw_ctx* c = pl.shots[s];
+    const int cx = (c->nx + pl.lx - 1) / pl.lx, cy = (c->ny + TY - 1) / TY, cz = (c->nz + kTZ - 1) / kTZ;
+    counts[s] = {cx, cy, cz};
+    shot_first[s] = (int)pl.units.size();
+    for (int i = 0; i < cx; ++i)
+      for (int j = 0; j < cy; ++j)
+        for (int k = 0; k < cz; ++k) {
+          Unit u{};
+          u.shot = (int)s;
+          u.x0 = i * pl.lx;
+          u.x1 = std::min(c->nx, (i + 1) * pl.lx);
+          u.y0 = j * TY;
+          u.z0 = k * kTZ;
+          pl.units.push_back(u);
+        }
+  }
+  shot_first[pl.shots.size()] = (int)pl.units.size();
+  const int U = (int)pl.units.size();
+  auto unit_of = [&](int s, int x, int y, int z) {
+    const auto& n = counts[s];
+    return shot_first[s] + ((x / pl.lx) * n[1] + y / TY) * n[2] + z / kTZ;
+  };
+  pl.max_rec = pl.max_src = 0;
+  pl.max_points = 0;
+  for (auto* c : pl.shots) {
+    pl.max_rec = std::max(pl.max_rec, c->rec.n);
+    pl.max_src = std::max(pl.max_src, c->src.n);
+    pl.max_points = std::max(pl.max_points, (long long)c->nx * c->ny * c->nz);
+  }
+  for (int role = 0; role < kNumRoles; ++role) {
+    RoleLists& L = pl.lists[role];
+    L = RoleLists();
+    // injection: (unit, x, y, z) -> terms (j, w), deterministic order
+    std::map<std::tuple<int, int, int, int>, std::vector<InjTerm>> inj;
+    std::vector<std::vector<int>> smp(U);
+    for (size_t s = 0; s < pl.shots.size(); ++s) {
+      const fdw_ctx* c = pl.shots[s];
+      const PointSet& ip = (role == kRoleAdj) ? c->rec : c->src;
+      for (int j = 0; j < ip.n; ++j)
+        for (int cc = 0; cc < 8; ++cc) {
+          const float w = ip.w[(size_t)j * 8 + cc];
+          if (w == 0.f) continue;
+          const int x = ip.base[(size_t)j * 3] + ((cc >> 2) & 1);
+          const int y = ip.base[(size_t)j * 3 + 1] + ((cc >> 1) & 1);
+          const int z = ip.base[(size_t)j * 3 + 2] + (cc & 1);
+          inj[std::make_tuple(unit_of((int)s, x, y, z), x, y, z)].push_back(InjTerm{j, w});
+        }
+      if (role != kRoleRec) {
+        const PointSet& sp = (role == kRoleAdj) ? c->src : c->rec;
+        for (int j = 0; j < sp.n; ++j) {
+          const int* b = &sp.base[(size_t)j * 3];
+          smp[unit_of((int)s, b[0], b[1], b[2])].push_back(j);
+        }
+      }
+    }
+    L.inj_ptr.assign(U + 1, 0);
+    for (auto& kv : inj) {
+      InjNode nd{};
+      nd.x = std::get<1>(kv.first);
+      nd.y = std::get<2>(kv.first);
+      nd.z = std::get<3>(kv.first);
+      nd.tbeg = (int)L.terms.size();
+      for (auto& t2 : kv.second) L.terms.push_back(t2);
+      nd.tend = (int)L.terms.size();
+      L.nodes.push_back(nd);
+      L.inj_ptr[std::get<0>(kv.first) + 1]++;
+    }
+    for (int u = 0; u < U; ++u) L.inj_ptr[u + 1] += L.inj_ptr[u];
+    L.smp_ptr.assign(U + 1, 0);
+    for (int u = 0; u < U; ++u) {
+      L.smp_ptr[u + 1] = L.smp_ptr[u] + (int)smp[u].size();
+      for (int j : smp[u]) L.smp_pts.push_back(j);
+    }
+    upload_vec((void**)&L.d_inj_ptr, L.inj_ptr.data(), L.inj_ptr.size() * sizeof(int));
+    upload_vec((void**)&L.d_smp_ptr, L.smp_ptr.data(), L.smp_ptr.size() * sizeof(int));
+    upload_vec((void**)&L.d_smp_pts, L.smp_pts.data(), L.smp_pts.size() * sizeof(int));
+    upload_vec((void**)&L.d_nodes, L.nodes.data(), L.nodes.size() * sizeof(InjNode));
+    upload_vec((void**)&L.d_terms, L.terms.data(), L.terms.size() * sizeof(InjTerm));
+  }
+  upload_vec((void**)&pl.d_units, pl.units.data(), pl.units.size() * sizeof(Unit));
+}
+
+// Descriptor of one shot for one role; data pointers are filled per call.
+static ShotDesc make_desc(const Plan& pl, fdw_ctx* c, int role) {
+  ShotDesc d;
+  std::memset(&d, 0, sizeof(d));
+  const TileShape t = kTiles[pl.tile];
+  const int TY = t.ny_pts * t.warps;
+  const int R4 = (pl.r + 3) & ~3;
+  float* ubuf = nullptr;
+  int uslots = 2;
+  if (role == kRoleFwd) ubuf = c->u;
+  else if (role == kRoleAdj) ubuf = c->lam;
+  else { ubuf = c->seg; uslots = c->seg_slots; }
+  d.nx = c->nx; d.ny = c->ny; d.nz = c->nz; d.nzp = c->nzp;
+  d.mtype = c->mtype;
+  d.u = ubuf;
+  d.uslot = c->slot;
+  if (ubuf) {
+    make_map(&d.tm_uh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ubuf, c->nx, c->ny, c->nz, c->nzp, uslots,
+             c->slot, kTZ + 2 * R4, TY + 2 * pl.r);
+    make_map(&d.tm_uc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ubuf, c->nx, c->ny, c->nz, c->nzp, uslots,
+             c->slot, kTZ, TY);
+  }
+  const CUtensorMapDataType mdt = c->mtype == kF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                  : c->mtype == kBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  make_map(&d.tm_m, mdt, msize(c->mtype), c->m, c->nx, c->ny, c->nz, c->nzp, 0, c->slot, kTZ, TY);
+  if (role == kRoleAdj && c->seg) {
+    make_map(&d.tm_f, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->seg, c->nx, c->ny, c->nz, c->nzp,
+             c->seg_slots, c->slot, kTZ, TY);
+    d.fwd = c->seg;
+    d.fslot = c->slot;
+    d.acc = c->acc;
+  }
+  if (c->use_etaf) {
+    make_map(&d.tm_e, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->etaf, c->nx, c->ny, c->nz, c->nzp, 0,
+             c->slot, kTZ, TY);
+    d.etaf = c->etaf;
+  }
+  d.m = c->m;
+  d.eta = c->eta;
+  const PointSet& sp = (role == kRoleAdj) ? c->src : c->rec;
+  if (role != kRoleRec) {
+    d.pt_base = sp.d_base;
+    d.pt_w = sp.d_w;
+    d.smp_n = sp.n;
+    d.smp_ld = sp.n;
+  }
+  d.inj_ld = (role == kRoleAdj) ? c->rec.n : c->src.n;
+  return d;
+}
+
+static std::vector<int> current_versions(const Plan& pl) {
+  std::vector<int> v;
+  for (auto* c : pl.shots) {
+    v.push_back(c->points_version);
+    v.push_back(c->buffers_version);
+    v.push_back(c->mtype);
+    v.push_back(c->use_etaf ? 1 : 0);
+  }
+  return v;
+}
+
+// (Re)build units, lists and descriptors when points, buffers or tiling changed.
+static void ensure_plan(Plan& pl) {
+  set_device(pl.device);
+  if (!pl.cap) CK(cudaStreamCreateWithFlags(&pl.cap, cudaStreamNonBlocking));
+  if (!pl.d_err) {
+    pl.d_err = dalloc<int>(1);
+    CK(cudaMemset(pl.d_err, 0, sizeof(int)));
+  }
+  const std::vector<int> v = current_versions(pl);
+  if (pl.built && v == pl.built_versions) return;
+  if (!pl.built) choose_default_tiling(pl);
+  build_lists(pl);
+  for (int role = 0; role < kNumRoles; ++role) {
+    pl.hdesc[role].clear();
+    for (auto* c : pl.shots) pl.hdesc[role].push_back(make_desc(pl, c, role));
+    dfree(pl.d_desc[role]);
+    pl.d_desc[role] = dalloc<ShotDesc>(pl.shots.size());
+    CK(cudaMemcpy(pl.d_desc[role], pl.hdesc[role].data(), sizeof(ShotDesc) * pl.shots.size(),
+                  cudaMemcpyHostToDevice));
+  }
+  pl.aux_version = -1;
+  pl.built_versions = v;
+  pl.built = true;
+}
+
+static void upload_desc(Plan& pl, int role, cudaStream_t s) {
+  CK(cudaMemcpyAsync(pl.d_desc[role], pl.hdesc[role].data(), sizeof(ShotDesc) * pl.shots.size(),
+                     cudaMemcpyHostToDevice, s));
+}
+
+// ---------------------------------------------------------------- launches
+
+struct StepArgs {
+  int role;
+  int cur, prev, out, fslot;
+  int inj_row, smp_row;
+  int flags;
+  bool grad;
+};
+
+static const Plan::LaunchInfo& launch_info(Plan& pl, bool grad) {
+  const bool etaf = plan_etaf(pl);
+  const int mt = plan_mtype(pl);
+  const int nunits = (int)pl.units.size();
+  auto key = std::make_tuple(pl.tile, pl.stages, (int)grad, (int)etaf, mt, nunits);
+  auto it = pl.launch_cache.find(key);
+  if (it != pl.launch_cache.end()) return it->second;
+  const StageLayout L = stage_layout(pl.r, pl.tile, msize(mt), grad, etaf);
+  Plan::LaunchInfo li;
+  li.smem = smem_bytes(L, pl.stages);
+  li.fn = step_fn(pl.r, pl.tile, grad);
+  configure_kernel(li.fn, li.smem);
+  int nb = 0;
+  li.threads = (kTiles[pl.tile].warps + 1) * 32;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, li.fn, li.threads, li.smem));
+  li.grid = std::max(1, std::min(nunits, std::max(nb, 1) * device_sms(pl.device)));
+  li.stage_bytes = L.bytes;
+  li.off_p = L.off_p;
+  li.off_m = L.off_m;
+  li.off_f = L.off_f;
+  li.off_e = L.off_e;
+  return pl.launch_cache.emplace(key, li).first->second;
+}
+
+static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s) {
+  const fdw_ctx* c0 = pl.shots[0];
+  const bool etaf = plan_etaf(pl);
+  const Plan::LaunchInfo& li = launch_info(pl, a.grad);
+  const int nunits = (int)pl.units.size();
+  if (pl.weights.empty()) pl.weights = fornberg_second_derivative(c0->order);
+
+  StepParams P;
+  std::memset(&P, 0, sizeof(P));
+  const RoleLists& Ls = pl.lists[a.role];
+  P.shots = pl.d_desc[a.role];
+  P.units = pl.d_units;
+  P.nunits = nunits;
+  P.flags = a.flags | (etaf ? kEtaField : 0);
+  P.inj_ptr = Ls.d_inj_ptr;
+  P.inj_nodes = Ls.d_nodes;
+  P.inj_terms = Ls.d_terms;
+  P.smp_ptr = Ls.d_smp_ptr;
+  P.smp_pts = Ls.d_smp_pts;
+  P.inj_row = a.inj_row;
+  P.smp_row = a.smp_row;
+  P.cur = a.cur;
+  P.prev = a.prev;
+  P.out = a.out;
+  P.fslot = a.fslot;
+  P.stages = pl.stages;
+  P.stage_bytes = li.stage_bytes;
+  P.off_p = li.off_p;
+  P.off_m = li.off_m;
+  P.off_f = li.off_f;
+  P.off_e = li.off_e;
+  const double dt = c0->dt;
+  P.dt2 = (float)(dt * dt);
+  const std::vector<double>& cw = pl.weights;
+  double csum = 0.0;
+  for (int ax = 0; ax < 3; ++ax) {
+    const bool active = !(c0->ny == 1 && c0->ndim == 2 && ax == 1);
+    const double sc = active ? dt * dt / (c0->h[ax] * c0->h[ax]) : 0.0;
+    for (int k = 0; k <= kMaxR; ++k) P.w[ax][k] = (k <= pl.r) ? (float)(cw[k] * sc) : 0.f;
+    csum += cw[0] * sc;
+  }
+  P.csum = (float)csum;
+  P.err = pl.d_err;
+
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(li.grid);
+  cfg.blockDim = dim3(li.threads);
+  cfg.dynamicSmemBytes = li.smem;
+  cfg.stream = s;
+  void* args[] = {&P};
+  CK(cudaLaunchKernelExC(&cfg, li.fn, args));
+}
+
+// Run `body` on stream s, through a cached CUDA graph unless FDW_NO_GRAPH is set.
+template <class F>
+static void run_graph(Plan& pl, const std::string& key, cudaStream_t s, F&& body) {
+  if (env_flag("FDW_NO_GRAPH")) {
+    body(s);
+    return;
+  }
+  auto it = pl.graphs.find(key);
+  if (it == pl.graphs.end()) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(pl.cap, cudaStreamCaptureModeThreadLocal));
+    try {
+      body(pl.cap);
+    } catch (...) {
+      cudaStreamEndCapture(pl.cap, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    CK(cudaStreamEndCapture(pl.cap, &g));
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    cuda_check(e, "cudaGraphInstantiate");
+    it = pl.graphs.emplace(key, ge).first;
+  }
+  CK(cudaGraphLaunch(it->second, s));
+}
+
+// ---------------------------------------------------------------- passes
+
+// Forward time loop over all shots of a plan; snapshots every k steps if k > 0.
+static void forward_body(Plan& pl, int k, int stype, cudaStream_t s) {
+  const int nt = pl.shots[0]->nt;
+  for (auto* c : pl.shots) CK(cudaMemsetAsync(c->u, 0, sizeof(float) * 2 * c->slot, s));
+  int flags_base = 0;
+  if (pl.max_src > 0) flags_base |= kInject;
+  if (pl.max_rec > 0) flags_base |= kSample;
+  const int nsnap = k > 0 ? (nt - 1) / k : 0;
+  if (nsnap > 0)
+    for (auto* c : pl.shots) CK(cudaMemsetAsync(c->amax, 0, sizeof(unsigned) * nsnap, s));
+  for (int n = 0; n + 1 < nt; ++n) {
+    StepArgs a{kRoleFwd, n & 1, (n + 1) & 1, (n + 1) & 1, 0, n, n, flags_base, false};
+    launch_step(pl, a, s);
+    if (k > 0 && (n + 1) % k == 0 && (n + 1) / k <= nsnap) {
+      const int j = (n + 1) / k;  // snapshot j holds (u^{jk}, u^{jk-1})
+      const size_t ns = pl.shots.size();
+      CK(launch_absmax(pl.d_pack + (size_t)(j - 1) * ns, (int)ns, pl.max_points, s));
+      CK(launch_pack(pl.d_pack + (size_t)(j - 1) * ns, (int)ns, pl.max_points, stype, s));
+    }
+  }
+  if (pl.max_rec > 0)
+    CK(launch_sample(pl.d_desc[kRoleFwd], (int)pl.shots.size(), pl.max_rec, (nt - 1) & 1, nt - 1, s));
+}
+
+static void adjoint_body(Plan& pl, cudaStream_t s) {
+  const int nt = pl.shots[0]->nt;
+  for (auto* c : pl.shots) CK(cudaMemsetAsync(c->lam, 0, sizeof(float) * 2 * c->slot, s));
+  int flags = 0;
+  if (pl.max_rec > 0) flags |= kInject;
+  if (pl.max_src > 0) flags |= kSample;
+  for (int k = nt - 1; k >= 1; --k) {
+    StepArgs a{kRoleAdj, (k + 1) & 1, k & 1, k & 1, 0, k, k, flags, false};
+    launch_step(pl, a, s);
+  }
+  if (pl.max_src > 0)
+    CK(launch_sample(pl.d_desc[kRoleAdj], (int)pl.shots.size(), pl.max_src, 1, 0, s));
+}
+
+static void gradient_body(Plan& pl, int k, int stype, bool diff, cudaStream_t s) {
+  const int nt = pl.shots[0]->nt;
+  const size_t ns = pl.shots.size();
+  for (auto* c : pl.shots) {
+    CK(cudaMemsetAsync(c->lam, 0, sizeof(float) * 2 * c->slot, s));
+    CK(cudaMemsetAsync(c->acc, 0, sizeof(float) * c->slot, s));
+  }
+  const int adj_flags = (pl.max_rec > 0 ? kInject : 0) | (diff ? kInjectDiff : 0);
+  const int rec_flags = pl.max_src > 0 ? kInject : 0;
+  const int nseg = (nt + k - 1) / k;
+  for (int j = nseg - 1; j >= 0; --j) {
+    const int a0 = j * k, b0 = std::min((j + 1) * k, nt);
+    if (j == 0) {
+      for (auto* c : pl.shots) CK(cudaMemsetAsync(c->seg, 0, sizeof(float) * 2 * c->slot, s));
+    } else {
+      CK(launch_unpack(pl.d_unpack + (size_t)(j - 1) * ns, (int)ns, pl.max_points, stype, s));
+    }
+    // recompute u^{a0+1} .. u^{b0-1}; slot i holds u^{a0-1+i}
+    for (int n = a0; n <= b0 - 2; ++n) {
+      StepArgs a{kRoleRec, n - a0 + 1, n - a0, n - a0 + 2, 0, n, 0, rec_flags, false};
+      launch_step(pl, a, s);
+    }
+    // adjoint steps with the imaging condition
+    for (int kk = b0 - 1; kk >= std::max(a0, 1); --kk) {
+      StepArgs a{kRoleAdj, (kk + 1) & 1, kk & 1, kk & 1, kk - a0 + 1, kk, 0, adj_flags, true};
+      launch_step(pl, a, s);
+    }
+  }
+}
+
+// Checkpoint buffers of a context for k and snapshot type.
+static void ensure_ckpt(fdw_ctx* c, int k, int stype) {
+  const int nsnap = (c->nt - 1) / k;
+  const long long pts = (long long)c->nx * c->ny * c->nz;
+  if (c->ckpt_k != k || c->snap_type != stype || !c->seg) {
+    dfree(c->snaps); dfree(c->amax); dfree(c->seg);
+    c->snaps = nullptr; c->amax = nullptr; c->seg = nullptr;
+    c->have_ckpt = false;
+    const size_t per = (size_t)pts * 2 * msize(stype);
+    c->snaps = dalloc<unsigned char>(std::max<size_t>(1, per * (size_t)nsnap));
+    c->amax = dalloc<unsigned int>(std::max(1, nsnap));
+    c->seg_slots = k + 1;
+    c->seg = dalloc<float>((size_t)c->slot * c->seg_slots);
+    c->ckpt_k = k;
+    c->snap_type = stype;
+    c->nsnap = nsnap;
+    c->buffers_version++;
+  }
+  if (!c->lam) {
+    c->lam = dalloc<float>((size_t)c->slot * 2);
+    c->buffers_version++;
+  }
+  if (!c->acc) {
+    c->acc = dalloc<float>((size_t)c->slot);
+    c->buffers_version++;
+  }
+  if (!c->qsave) {
+    c->qsave = dalloc<float>(std::max<size_t>(1, (size_t)c->nt * std::max(1, c->src.n)));
+  }
+}
+
+static void ensure_aux(Plan& pl) {
+  const int k = pl.shots[0]->ckpt_k;
+  const int nsnap = pl.shots[0]->nsnap;
+  const int ver = pl.shots[0]->buffers_version * 131 + k;
+  if (pl.aux_version == ver && pl.d_pack) return;
+  const size_t ns = pl.shots.size();
+  std::vector<AuxShot> pack((size_t)std::max(nsnap, 1) * ns), unpack(pack.size());
+  for (int j = 1; j <= nsnap; ++j)
+    for (size_t s = 0; s < ns; ++s) {
+      fdw_ctx* c = pl.shots[s];
+      const long long pts = (long long)c->nx * c->ny * c->nz;
+      const size_t per = (size_t)pts * 2 * msize(c->snap_type);
+      AuxShot a;
+      a.g = Geom{c->nx, c->ny, c->nz, c->nzp};
+      a.snap = static_cast<unsigned char*>(c->snaps) + per * (size_t)(j - 1);
+      a.amax = c->amax + (j - 1);
+      a.a = c->u + (size_t)((j * k) & 1) * c->slot;       // u^{jk}
+      a.b = c->u + (size_t)((j * k - 1) & 1) * c->slot;   // u^{jk-1}
+      pack[(size_t)(j - 1) * ns + s] = a;
+      a.a = c->seg + c->slot;   // slot 1: u^{a0}
+      a.b = c->seg;             // slot 0: u^{a0-1}
+      unpack[(size_t)(j - 1) * ns + s] = a;
+    }
+  upload_vec((void**)&pl.d_pack, pack.data(), pack.size() * sizeof(AuxShot));
+  upload_vec((void**)&pl.d_unpack, unpack.data(), unpack.size() * sizeof(AuxShot));
+  pl.aux_version = ver;
+}
+
+// ---------------------------------------------------------------- call helpers
+
+template <class F>
+static fdw_status guard(std::string* err, F&& f) {
+  try {
+    f();
+    if (err) err->clear();
+    return FDW_OK;
+  } catch (const Error& e) {
+    if (err) *err = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    if (err) *err = "host out of memory";
+    return FDW_ERR_OOM;
+  } catch (...) {
+    if (err) *err = "unknown error";
+    return FDW_ERR_CUDA;
+  }
+}
+
+static Plan& ctx_plan(fdw_ctx* c) {
+  if (!c->plan) {
+    c->plan.reset(new Plan());
+    c->plan->shots = {c};
+    c->plan->device = c->device;
+    c->plan->r = c->r;
+    c->plan->tile_req = c->tile;
+    c->plan->lx_req = c->xchunk;
+    c->plan->stages_req = c->stages;
+  }
+  ensure_plan(*c->plan);
+  return *c->plan;
+}
+
+static void require_model(const fdw_ctx* c) {
+  if (!c->model_set) fail(FDW_ERR_STATE, "model not set (fdw_set_model)");
+}
+
+static void check_compatible(const std::vector<fdw_ctx*>& v) {
+  const fdw_ctx* a = v[0];
+  for (auto* c : v) {
+    if (c->order != a->order || c->nt != a->nt || c->dt != a->dt || c->mtype != a->mtype ||
+        c->device != a->device || c->ndim != a->ndim)
+      fail(FDW_ERR_ARG, "batched contexts must share order, dt, nt, ndim, device and model type");
+    for (int ax = 0; ax < 3; ++ax)
+      if (c->h[ax] != a->h[ax]) fail(FDW_ERR_ARG, "batched contexts must share the grid spacing");
+    require_model(c);
+  }
+}
+
+// Forward over a plan's shots with per-shot q / rec (host or device).
+static void plan_forward(Plan& pl, const float* const* q, float* const* rec, int k, int stype,
+                         cudaStream_t s) {
+  const size_t ns = pl.shots.size();
+  std::vector<std::pair<float*, float*>> copies;  // (host dst, staging src)
+  std::vector<size_t> sizes;
+  for (size_t i = 0; i < ns; ++i) {
+    fdw_ctx* c = pl.shots[i];
+    const size_t nq = (size_t)c->nt * c->src.n, nr = (size_t)c->nt * c->rec.n;
+    if (c->src.n > 0 && !q[i]) fail(FDW_ERR_ARG, "source wavelet array is null");
+    if (c->rec.n > 0 && !rec[i]) fail(FDW_ERR_ARG, "receiver output array is null");
+    const float* qd = device_in(c, 1, q[i], nq, s);
+    bool host = false;
+    float* rd = device_out(c, 2, rec[i], nr, &host);
+    if (host) {
+      copies.push_back({rec[i], rd});
+      sizes.push_back(nr);
+    }
+    pl.hdesc[kRoleFwd][i].inj_a = qd;
+    pl.hdesc[kRoleFwd][i].inj_b = nullptr;
+    pl.hdesc[kRoleFwd][i].smp_out = rd;
+    if (k > 0 && nq > 0) CK(cudaMemcpyAsync(c->qsave, qd, nq * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  }
+  upload_desc(pl, kRoleFwd, s);
+  if (k > 0) {
+    ensure_aux(pl);
+    for (size_t i = 0; i < ns; ++i) pl.hdesc[kRoleRec][i].inj_a = pl.shots[i]->qsave;
+    upload_desc(pl, kRoleRec, s);
+  }
+  std::ostringstream key;
+  key << "fwd k" << k << " t" << stype;
+  run_graph(pl, key.str(), s, [&](cudaStream_t st) { forward_body(pl, k, stype, st); });
+  for (size_t i = 0; i < copies.size(); ++i)
+    CK(cudaMemcpyAsync(copies[i].first, copies[i].second, sizes[i] * sizeof(float),
+                       cudaMemcpyDeviceToHost, s));
+  for (auto* c : pl.shots) {
+    c->fwd_done = true;
+    if (k > 0) c->have_ckpt = true;
+  }
+}
+
+static void plan_gradient(Plan& pl, const float* const* resid, const float* const* sub,
+                          float* const* grad, int layout, cudaStream_t s) {
+  const size_t ns = pl.shots.size();
+  bool diff = false;
+  for (size_t i = 0; i < ns; ++i) {
+    fdw_ctx* c = pl.shots[i];
+    if (!c->have_ckpt) fail(FDW_ERR_STATE, "no checkpointed forward to differentiate");
+    if (!grad[i]) fail(FDW_ERR_ARG, "gradient output is null");
+    if (c->rec.n > 0 && !resid[i]) fail(FDW_ERR_ARG, "residual array is null");
+    if (sub && sub[i]) diff = true;
+  }
+  for (size_t i = 0; i < ns; ++i) {
+    fdw_ctx* c = pl.shots[i];
+    const size_t nr = (size_t)c->nt * c->rec.n;
+    pl.hdesc[kRoleAdj][i].inj_a = device_in(c, 3, resid[i], nr, s);
+    const float* b = (sub && sub[i]) ? device_in(c, 4, sub[i], nr, s) : nullptr;
+    if (diff && !b) {  // keep one flag for the whole launch: subtract zeros
+      float* z = static_cast<float*>(staging_buf(c, 5, std::max<size_t>(nr, 1) * sizeof(float)));
+      CK(cudaMemsetAsync(z, 0, std::max<size_t>(nr, 1) * sizeof(float), s));
+      b = z;
+    }
+    pl.hdesc[kRoleAdj][i].inj_b = b;
+    pl.hdesc[kRoleAdj][i].smp_out = nullptr;
+  }
+  upload_desc(pl, kRoleAdj, s);
+  ensure_aux(pl);
+  const int k = pl.shots[0]->ckpt_k, stype = pl.shots[0]->snap_type;
+  std::ostringstream key;
+  key << "grad k" << k << " t" << stype << " d" << diff;
+  run_graph(pl, key.str(), s, [&](cudaStream_t st) { gradient_body(pl, k, stype, diff, st); });
+  for (size_t i = 0; i < ns; ++i) {
+    fdw_ctx* c = pl.shots[i];
+    const size_t nout = layout == FDW_LAYOUT_COMPUTATIONAL ? (size_t)c->nx * c->ny * c->nz
+                                                           : (size_t)c->phys[0] * c->phys[1] * c->phys[2];
+    bool host = false;
+    float* gd = device_out(c, 6, grad[i], nout, &host);
+    const double dt = c->dt;
+    CK(launch_grad_out(c->acc, Geom{c->nx, c->ny, c->nz, c->nzp}, (float)(-1.0 / (dt * dt)), gd,
+                       layout == FDW_LAYOUT_COMPUTATIONAL ? 1 : 0, c->nbl, c->ndim, (int)c->phys[0],
+                       (int)c->phys[1], (int)c->phys[2], s));
+    if (host) CK(cudaMemcpyAsync(grad[i], gd, nout * sizeof(float), cudaMemcpyDeviceToHost, s));
+  }
+}
+
+static void plan_sync(Plan& pl) {
+  set_device(pl.device);
+  CK(cudaDeviceSynchronize());
+  int e = 0;
+  if (pl.d_err) {
+    CK(cudaMemcpy(&e, pl.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+      CK(cudaMemset(pl.d_err, 0, sizeof(int)));
+      std::ostringstream os;
+      os << "device-side wait timed out (code " << e << ")";
+      fail(FDW_ERR_TIMEOUT, os.str());
+    }
+  }
+}
+
+// ---------------------------------------------------------------- autotune
+
+static std::string tune_key(const Plan& pl) {
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, pl.device));
+  std::ostringstream os;
+  os << prop.name << "|r" << pl.r << "|m" << plan_mtype(pl) << "|";
+  for (auto* c : pl.shots) os << c->nx << "x" << c->ny << "x" << c->nz << ";";
+  return os.str();
+}
+
+static bool tune_cache_lookup(const std::string& key, int* t, int* lx, int* st) {
+  const char* path = std::getenv("FDW_AUTOTUNE_CACHE");
+  if (!path || !*path) return false;
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) {
+    const size_t p = line.rfind('\t');
+    if (p == std::string::npos || line.substr(0, p) != key) continue;
+    return std::sscanf(line.c_str() + p + 1, "%d %d %d", t, lx, st) == 3;
+  }
+  return false;
+}
+
+static void tune_cache_store(const std::string& key, int t, int lx, int st) {
+  const char* path = std::getenv("FDW_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  std::ofstream f(path, std::ios::app);
+  f << key << "\t" << t << " " << lx << " " << st << "\n";
+}
+
+static void plan_autotune(Plan& pl, int steps) {
+  ensure_plan(pl);
+  const std::string key = tune_key(pl);
+  int bt = -1, blx = 0, bst = 0;
+  if (!tune_cache_lookup(key, &bt, &blx, &bst)) {
+    bool all2d = true;
+    int nxmax = 1;
+    for (auto* c : pl.shots) {
+      if (c->ny > 1) all2d = false;
+      nxmax = std::max(nxmax, c->nx);
+    }
+    std::vector<int> tiles = all2d ? std::vector<int>{3} : std::vector<int>{0, 1, 2};
+    std::vector<int> lxs = {8, 16, 24, 32, 48, 64, 96, 128, nxmax};
+    cudaStream_t s = pl.cap;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int t : tiles) {
+      const int ms = max_stages(pl, t);
+      for (int extra : {2, 3, 5}) {
+        const int st = std::min(pl.r + 1 + extra, ms);
+        for (int lx : lxs) {
+          if (lx > nxmax && lx != nxmax) continue;
+          pl.tile = t;
+          pl.lx = lx;
+          pl.stages = st;
+          build_lists(pl);
+          for (size_t i = 0; i < pl.shots.size(); ++i)
+            pl.hdesc[kRoleFwd][i] = make_desc(pl, pl.shots[i], kRoleFwd);
+          upload_desc(pl, kRoleFwd, s);
+          StepArgs a{kRoleFwd, 0, 1, 1, 0, 0, 0, 0, false};
+          for (int w = 0; w < 2; ++w) launch_step(pl, a, s);
+          CK(cudaEventRecord(e0, s));
+          for (int i = 0; i < steps; ++i) {
+            a.cur = i & 1; a.prev = a.out = (i + 1) & 1;
+            launch_step(pl, a, s);
+          }
+          CK(cudaEventRecord(e1, s));
+          CK(cudaEventSynchronize(e1));
+          float ms_ = 0.f;
+          CK(cudaEventElapsedTime(&ms_, e0, e1));
+          if (ms_ < best) {
+            best = ms_;
+            bt = t; blx = lx; bst = st;
+          }
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    plan_sync(pl);
+    tune_cache_store(key, bt, blx, bst);
+  }
+  pl.tile = bt;
+  pl.lx = blx;
+  pl.stages = bst;
+  pl.tile_req = bt;
+  pl.lx_req = blx;
+  pl.stages_req = bst;
+  pl.built = false;
+  ensure_plan(pl);
+}
+
+// ================================================================= C ABI
+
+extern "C" {
+
+int fdw_version(void) { return 100; }
+
+const char* fdw_status_string(fdw_status st) {
+  switch (st) {
+    case FDW_OK: return "ok";
+    case FDW_ERR_ARG: return "invalid argument";
+    case FDW_ERR_SHAPE: return "invalid shape";
+    case FDW_ERR_ORDER: return "invalid space order";
+    case FDW_ERR_CFL: return "time step above the stability limit";
+    case FDW_ERR_OUT_OF_DOMAIN: return "point outside the domain";
+    case FDW_ERR_OOM: return "out of memory";
+    case FDW_ERR_CUDA: return "CUDA error";
+    case FDW_ERR_TIMEOUT: return "device-side wait timed out";
+    case FDW_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+fdw_status fdw_fd_weights(int space_order, double* c) {
+  if (!valid_order(space_order)) return FDW_ERR_ORDER;
+  if (!c) return FDW_ERR_ARG;
+  const std::vector<double> w = fornberg_second_derivative(space_order);
+  for (size_t i = 0; i < w.size(); ++i) c[i] = w[i];
+  return FDW_OK;
+}
+
+double fdw_dt_max(int ndim, const double* spacing, int space_order, double vmax) {
+  if ((ndim != 2 && ndim != 3) || !spacing || !valid_order(space_order) || !(vmax > 0)) return -1.0;
+  for (int a = 0; a < ndim; ++a)
+    if (!(spacing[a] > 0)) return -1.0;
+  return dt_limit(ndim, spacing, space_order, vmax);
+}
+
+fdw_status fdw_create(fdw_ctx** out, int ndim, const int64_t* shape, const double* spacing,
+                      int space_order, int nbl, double dt, int nt, double vmax, int device) {
+  if (!out) return FDW_ERR_ARG;
+  *out = nullptr;
+  if (ndim != 2 && ndim != 3) return FDW_ERR_SHAPE;
+  if (!shape || !spacing) return FDW_ERR_ARG;
+  if (!valid_order(space_order)) return FDW_ERR_ORDER;
+  if (nbl < 0 || nt < 1 || !(dt > 0) || !(vmax > 0)) return FDW_ERR_ARG;
+  for (int a = 0; a < ndim; ++a) {
+    if (shape[a] < 2 || shape[a] + 2LL * nbl > (1LL << 20)) return FDW_ERR_SHAPE;
+    if (!(spacing[a] > 0)) return FDW_ERR_ARG;
+  }
+  if (dt > dt_limit(ndim, spacing, space_order, vmax)) return FDW_ERR_CFL;
+  std::unique_ptr<fdw_ctx> c(new fdw_ctx());
+  fdw_status st = guard(nullptr, [&] {
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) fail(FDW_ERR_CUDA, "no such CUDA device");
+    set_device(device);
+    c->device = device;
+    c->ndim = ndim;
+    if (ndim == 3) {
+      for (int a = 0; a < 3; ++a) { c->phys[a] = shape[a]; c->h[a] = spacing[a]; }
+    } else {
+      c->phys[0] = shape[0]; c->phys[1] = 1; c->phys[2] = shape[1];
+      c->h[0] = spacing[0]; c->h[1] = 1.0; c->h[2] = spacing[1];
+    }
+    c->order = space_order;
+    c->r = space_order / 2;
+    c->nbl = nbl;
+    c->dt = dt;
+    c->nt = nt;
+    c->vmax = vmax;
+    c->nx = (int)(c->phys[0] + 2 * nbl);
+    c->ny = ndim == 3 ? (int)(c->phys[1] + 2 * nbl) : 1;
+    c->nz = (int)(c->phys[2] + 2 * nbl);
+    c->nzp = (c->nz + 31) & ~31;
+    c->slot = (long long)c->nx * c->ny * c->nzp;
+    c->u = dalloc<float>((size_t)c->slot * 2);
+    c->m = dalloc<float>((size_t)c->slot);
+    CK(cudaMemset(c->u, 0, sizeof(float) * 2 * c->slot));
+    CK(cudaMemset(c->m, 0, sizeof(float) * c->slot));
+    // built-in damping profiles, eta * dt / 2
+    std::vector<float> prof((size_t)c->nx + c->ny + c->nz, 0.f);
+    const int n3[3] = {c->nx, c->ny, c->nz};
+    size_t off = 0;
+    for (int a = 0; a < 3; ++a) {
+      const bool active = !(ndim == 2 && a == 1);
+      for (int i = 0; i < n3[a]; ++i) {
+        double e = 0.0;
+        if (active && nbl > 0) {
+          const long long lo = nbl - i, hi = i - (nbl + c->phys[a] - 1);
+          const long long d = lo > 0 ? lo : (hi > 0 ? hi : 0);
+          const double emax = 3.0 * std::log(1000.0) / (2.0 * nbl * c->h[a] * vmax);
+          const double f = (double)d / nbl;
+          e = emax * f * f;
+        }
+        prof[off + i] = (float)(e * dt * 0.5);
+      }
+      off += n3[a];
+    }
+    c->eta = dalloc<float>(prof.size());
+    CK(cudaMemcpy(c->eta, prof.data(), prof.size() * sizeof(float), cudaMemcpyHostToDevice));
+  });
+  if (st != FDW_OK) return st;
+  *out = c.release();
+  return FDW_OK;
+}
+
+void fdw_destroy(fdw_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  delete ctx;
+}
+
+const char* fdw_last_error(const fdw_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+fdw_status fdw_set_model(fdw_ctx* c, const float* m, int layout, int m_dtype, void* stream) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    if (!m) fail(FDW_ERR_ARG, "model is null");
+    if (layout != FDW_LAYOUT_PHYSICAL && layout != FDW_LAYOUT_COMPUTATIONAL) fail(FDW_ERR_ARG, "bad layout");
+    if (m_dtype != kF32 && m_dtype != kF16 && m_dtype != kBF16) fail(FDW_ERR_ARG, "bad model type");
+    set_device(c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = layout == FDW_LAYOUT_PHYSICAL
+                         ? (size_t)c->phys[0] * c->phys[1] * c->phys[2]
+                         : (size_t)c->nx * c->ny * c->nz;
+    const float* md = device_in(c, 7, m, n, s);
+    if (m_dtype != c->mtype) {
+      dfree(c->m);
+      c->m = nullptr;
+      c->m = dalloc<unsigned char>((size_t)c->slot * msize(m_dtype));
+      CK(cudaMemsetAsync(c->m, 0, (size_t)c->slot * msize(m_dtype), s));
+      c->mtype = m_dtype;
+      c->buffers_version++;
+    }
+    CK(launch_model(md, layout == FDW_LAYOUT_PHYSICAL ? 0 : 1, (int)c->phys[0], (int)c->phys[1],
+                    (int)c->phys[2], c->nbl, c->ndim, c->m, c->mtype,
+                    Geom{c->nx, c->ny, c->nz, c->nzp}, s));
+    c->model_set = true;
+  });
+}
+
+fdw_status fdw_set_damping(fdw_ctx* c, const float* eta, void* stream) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    set_device(c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!eta) {
+      if (c->use_etaf) {
+        c->use_etaf = false;
+        c->buffers_version++;
+      }
+      return;
+    }
+    if (!c->etaf) {
+      c->etaf = dalloc<float>((size_t)c->slot);
+      CK(cudaMemsetAsync(c->etaf, 0, sizeof(float) * c->slot, s));
+    }
+    const float* ed = device_in(c, 8, eta, (size_t)c->nx * c->ny * c->nz, s);
+    CK(launch_eta_field(ed, (float)(0.5 * c->dt), c->etaf, Geom{c->nx, c->ny, c->nz, c->nzp}, s));
+    if (!c->use_etaf) {
+      c->use_etaf = true;
+      c->buffers_version++;
+    }
+  });
+}
+
+fdw_status fdw_set_sources(fdw_ctx* c, int nsrc, const double* xyz) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    set_device(c->device);
+    compute_points(c, c->src, nsrc, xyz);
+    dfree(c->qsave);
+    c->qsave = nullptr;
+    c->have_ckpt = false;
+  });
+}
+
+fdw_status fdw_set_receivers(fdw_ctx* c, int nrec, const double* xyz) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    set_device(c->device);
+    compute_points(c, c->rec, nrec, xyz);
+  });
+}
+
+fdw_status fdw_forward(fdw_ctx* c, const float* q, float* rec, void* stream) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    require_model(c);
+    set_device(c->device);
+    Plan& pl = ctx_plan(c);
+    plan_forward(pl, &q, &rec, 0, 0, static_cast<cudaStream_t>(stream));
+  });
+}
+
+fdw_status fdw_forward_ckpt(fdw_ctx* c, const float* q, float* rec, int k, int stype, void* stream) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    require_model(c);
+    if (k < 1) fail(FDW_ERR_ARG, "ckpt_every must be >= 1");
+    if (stype != kF32 && stype != kF16 && stype != kBF16) fail(FDW_ERR_ARG, "bad snapshot type");
+    set_device(c->device);
+    ensure_ckpt(c, k, stype);
+    Plan& pl = ctx_plan(c);
+    plan_forward(pl, &q, &rec, k, stype, static_cast<cudaStream_t>(stream));
+  });
+}
+
+fdw_status fdw_adjoint(fdw_ctx* c, const float* d, float* qadj, void* stream) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    require_model(c);
+    set_device(c->device);
+    if (!c->lam) {
+      c->lam = dalloc<float>((size_t)c->slot * 2);
+      c->buffers_version++;
+    }
+    Plan& pl = ctx_plan(c);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t nd = (size_t)c->nt * c->rec.n, nq = (size_t)c->nt * c->src.n;
+    if (c->rec.n > 0 && !d) fail(FDW_ERR_ARG, "data array is null");
+    if (c->src.n > 0 && !qadj) fail(FDW_ERR_ARG, "output array is null");
+    bool host = false;
+    pl.hdesc[kRoleAdj][0].inj_a = device_in(c, 3, d, nd, s);
+    pl.hdesc[kRoleAdj][0].inj_b = nullptr;
+    float* qo = device_out(c, 9, qadj, nq, &host);
+    pl.hdesc[kRoleAdj][0].smp_out = qo;
+    upload_desc(pl, kRoleAdj, s);
+    run_graph(pl, "adj", s, [&](cudaStream_t st) { adjoint_body(pl, st); });
+    if (host) CK(cudaMemcpyAsync(qadj, qo, nq * sizeof(float), cudaMemcpyDeviceToHost, s));
+    c->adj_done = true;
+  });
+}
+
+fdw_status fdw_gradient(fdw_ctx* c, const float* resid, const float* resid_sub, float* grad,
+                        int layout, void* stream) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    require_model(c);
+    if (layout != FDW_LAYOUT_PHYSICAL && layout != FDW_LAYOUT_COMPUTATIONAL) fail(FDW_ERR_ARG, "bad layout");
+    set_device(c->device);
+    Plan& pl = ctx_plan(c);
+    plan_gradient(pl, &resid, &resid_sub, &grad, layout, static_cast<cudaStream_t>(stream));
+  });
+}
+
+fdw_status fdw_get_wavefield(fdw_ctx* c, int which, float* out, void* stream) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    if (!out) fail(FDW_ERR_ARG, "output is null");
+    set_device(c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const float* src = nullptr;
+    if (which == 0) {
+      if (!c->fwd_done) fail(FDW_ERR_STATE, "no forward run yet");
+      src = c->u + (size_t)((c->nt - 1) & 1) * c->slot;
+    } else if (which == 1) {
+      if (!c->adj_done) fail(FDW_ERR_STATE, "no adjoint run yet");
+      src = c->lam + c->slot;
+    } else {
+      fail(FDW_ERR_ARG, "which must be 0 or 1");
+    }
+    const size_t n = (size_t)c->nx * c->ny * c->nz;
+    bool host = false;
+    float* od = device_out(c, 10, out, n, &host);
+    CK(launch_copy_out(src, Geom{c->nx, c->ny, c->nz, c->nzp}, od, s));
+    if (host) CK(cudaMemcpyAsync(out, od, n * sizeof(float), cudaMemcpyDeviceToHost, s));
+  });
+}
+
+fdw_status fdw_sync(fdw_ctx* c) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    if (c->plan) plan_sync(*c->plan);
+    else {
+      set_device(c->device);
+      CK(cudaDeviceSynchronize());
+    }
+  });
+}
+
+fdw_status fdw_autotune(fdw_ctx* c, int steps) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    require_model(c);
+    set_device(c->device);
+    Plan& pl = ctx_plan(c);
+    plan_autotune(pl, std::max(1, steps));
+    c->fwd_done = false;
+  });
+}
+
+fdw_status fdw_set_tiling(fdw_ctx* c, int tile, int xchunk, int stages) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    if (tile < -1 || tile >= kNumTiles) fail(FDW_ERR_ARG, "tile index out of range");
+    if (xchunk < 0 || stages < 0) fail(FDW_ERR_ARG, "negative tiling value");
+    if (stages > 0 && stages < c->r + 2) fail(FDW_ERR_ARG, "stages must be >= r + 2");
+    c->tile = tile;
+    c->xchunk = xchunk;
+    c->stages = stages;
+    c->plan.reset();
+  });
+}
+
+fdw_status fdw_get_tiling(fdw_ctx* c, int* out5) {
+  if (!c || !out5) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    Plan& pl = ctx_plan(c);
+    out5[0] = pl.tile;
+    out5[1] = pl.lx;
+    out5[2] = pl.stages;
+    out5[3] = std::min((int)pl.units.size(), resident_ctas(pl, pl.tile, pl.stages, false));
+    out5[4] = (int)pl.units.size();
+  });
+}
+
+fdw_status fdw_batch_create(fdw_batch** out, int nshots, fdw_ctx* const* ctxs) {
+  if (!out || nshots < 1 || !ctxs) return FDW_ERR_ARG;
+  *out = nullptr;
+  std::unique_ptr<fdw_batch> b(new fdw_batch());
+  fdw_status st = guard(&b->err, [&] {
+    for (int i = 0; i < nshots; ++i) {
+      if (!ctxs[i]) fail(FDW_ERR_ARG, "null context in batch");
+      b->shots.push_back(ctxs[i]);
+    }
+    check_compatible(b->shots);
+    b->plan.reset(new Plan());
+    b->plan->shots = b->shots;
+    b->plan->device = b->shots[0]->device;
+    b->plan->r = b->shots[0]->r;
+  });
+  if (st != FDW_OK) return st;
+  *out = b.release();
+  return FDW_OK;
+}
+
+void fdw_batch_destroy(fdw_batch* b) {
+  if (!b) return;
+  if (!b->shots.empty()) {
+    cudaSetDevice(b->shots[0]->device);
+    cudaDeviceSynchronize();
+  }
+  delete b;
+}
+
+const char* fdw_batch_last_error(const fdw_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+fdw_status fdw_batch_forward(fdw_batch* b, const float* const* q, float* const* rec, void* stream) {
+  if (!b || !q || !rec) return FDW_ERR_ARG;
+  return guard(&b->err, [&] {
+    check_compatible(b->shots);
+    ensure_plan(*b->plan);
+    plan_forward(*b->plan, q, rec, 0, 0, static_cast<cudaStream_t>(stream));
+  });
+}
+
+fdw_status fdw_batch_forward_ckpt(fdw_batch* b, const float* const* q, float* const* rec, int k,
+                                  int stype, void* stream) {
+  if (!b || !q || !rec) return FDW_ERR_ARG;
+  return guard(&b->err, [&] {
+    if (k < 1) fail(FDW_ERR_ARG, "ckpt_every must be >= 1");
+    if (stype != kF32 && stype != kF16 && stype != kBF16) fail(FDW_ERR_ARG, "bad snapshot type");
+    check_compatible(b->shots);
+    set_device(b->plan->device);
+    for (auto* c : b->shots) ensure_ckpt(c, k, stype);
+    ensure_plan(*b->plan);
+    plan_forward(*b->plan, q, rec, k, stype, static_cast<cudaStream_t>(stream));
+  });
+}
+
+fdw_status fdw_batch_gradient(fdw_batch* b, const float* const* resid, const float* const* sub,
+                              float* const* grad, int layout, void* stream) {
+  if (!b || !resid || !grad) return FDW_ERR_ARG;
+  return guard(&b->err, [&] {
+    if (layout != FDW_LAYOUT_PHYSICAL && layout != FDW_LAYOUT_COMPUTATIONAL) fail(FDW_ERR_ARG, "bad layout");
+    check_compatible(b->shots);
+    ensure_plan(*b->plan);
+    plan_gradient(*b->plan, resid, sub, grad, layout, static_cast<cudaStream_t>(stream));
+  });
+}
+
+fdw_status fdw_batch_autotune(fdw_batch* b, int steps) {
+  if (!b) return FDW_ERR_ARG;
+  return guard(&b->err, [&] {
+    check_compatible(b->shots);
+    plan_autotune(*b->plan, std::max(1, steps));
+  });
+}
+
+fdw_status fdw_batch_get_tiling(fdw_batch* b, int* out5) {
+  if (!b || !out5) return FDW_ERR_ARG;
+  return guard(&b->err, [&] {
+    Plan& pl = *b->plan;
+    ensure_plan(pl);
+    out5[0] = pl.tile;
+    out5[1] = pl.lx;
+    out5[2] = pl.stages;
+    out5[3] = std::min((int)pl.units.size(), resident_ctas(pl, pl.tile, pl.stages, false));
+    out5[4] = (int)pl.units.size();
+  });
+}
+
+}  // extern "C"

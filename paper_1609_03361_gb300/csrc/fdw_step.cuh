@@ -1,0 +1,302 @@
+// One explicit time step of the damped acoustic wave equation
+//     m u_tt + eta u_t - lap(u) = q                      (paper Sec. 5, Eq. 3)
+// in the three-level form
+//     u^{n+1} = [ 2 m u^n - (m - eta dt/2) u^{n-1} + dt^2 L u^n ] / (m + eta dt/2)
+// (centred u_tt as in the `dt2` expansion of Sec. 3.1, centred u_t for the
+// damping term, order-p Laplacian L with a zero halo), fused with the sparse
+// point-to-grid injection and grid-to-point sampling of Sec. 5.2.  The same
+// kernel performs the adjoint step of Sec. 5.1 (Listing 7): that recursion has
+// exactly this algebra with the roles of the time levels read backwards, so
+// only the wavefield slots and the point lists change.  With GRAD it also
+// accumulates the FWI imaging term u^k (lambda^k - 2 lambda^{k+1} + lambda^{k+2}).
+//
+// Layout: every field is [x][y][zp] (z contiguous, rows padded to zp), x the
+// slowest axis.  A CTA owns a column tile of TY x TZ points (y, z) and streams
+// along a chunk [x0, x1) of x:
+//  - a producer warp issues TMA loads, one pipeline stage per x plane: the
+//    u^n plane with its (r, R4) halo in y and z (zero-filled outside the grid,
+//    which is the zero halo of the scheme), and for computed planes the
+//    u^{n-1}, m (and forward-wavefield / damping) tiles;
+//  - consumer warps keep the 2r+1 values of u^n along x of their points in
+//    registers (a sliding queue), take y and z neighbours from shared memory,
+//    write u^{n+1} with coalesced stores and release the stage;
+//  - after the chunk, the consumers add the injected values into the nodes the
+//    unit owns (deterministic order, no atomics: no other CTA reads u^{n+1}
+//    during this step) and record the sampled points of u^n.
+#pragma once
+
+#include "fdw_device.cuh"
+
+namespace fdw {
+
+template <int R>
+struct Halo {
+  static constexpr int R4 = (R + 3) & ~3;  // z halo rounded up to 16 bytes (TMA x alignment)
+  static constexpr int ZW = kTZ + 2 * R4;  // staged row length
+};
+
+struct Cursor {
+  int stage;
+  uint32_t phase;
+  __device__ __forceinline__ void next(int S) {
+    if (++stage == S) { stage = 0; phase ^= 1u; }
+  }
+  __device__ __forceinline__ void skip(int k, int S) {  // k < S
+    stage += k;
+    if (stage >= S) { stage -= S; phase ^= 1u; }
+  }
+};
+
+__device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort) {
+#pragma unroll 1
+  for (int i = 0; i < 32; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  long long t0 = clock64();
+#pragma unroll 1
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitBudget) return false;
+  }
+}
+
+template <int R, int NY, int BY, bool GRAD>
+__global__ void __launch_bounds__((BY + 1) * 32)
+step_kernel(const __grid_constant__ StepParams P) {
+  constexpr int TZ = kTZ;
+  constexpr int TY = BY * NY;
+  constexpr int R4 = Halo<R>::R4;
+  constexpr int ZW = Halo<R>::ZW;
+  constexpr int YW = TY + 2 * R;
+  constexpr int NCONS = BY * 32;
+
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ int s_abort;
+  __shared__ int s_issued;
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const int S = P.stages;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * P.stage_bytes);
+  const uint32_t full0 = smem_u32(bars);
+  const uint32_t empty0 = smem_u32(bars + S);
+  const uint32_t tail = smem_u32(bars + 2 * S);  // consumer-only barrier at the end of a unit
+  volatile int* abort_flag = &s_abort;
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, BY);
+    }
+    mbar_init(tail, NCONS);
+    s_abort = 0;
+    s_issued = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  if (warp == BY) {
+    // ------------------------------ producer ------------------------------
+    if (lane == 0) {
+      Cursor c{0, 0u};
+      int issued = 0;
+      const uint32_t bytes_u = YW * ZW * 4;
+      for (int u = blockIdx.x; u < P.nunits && !*abort_flag; u += gridDim.x) {
+        const Unit un = P.units[u];
+        const ShotDesc* d = P.shots + un.shot;
+        const uint32_t bytes_in = TY * TZ * 4 + TY * TZ * (d->mtype == kF32 ? 4 : 2) +
+                                  (GRAD ? TY * TZ * 4 : 0) +
+                                  ((P.flags & kEtaField) ? TY * TZ * 4 : 0);
+        for (int p = un.x0 - R; p < un.x1 + R; ++p) {
+          const uint32_t full = full0 + 8 * c.stage, empty = empty0 + 8 * c.stage;
+          if (issued >= S && !wait_or_abort(empty, c.phase ^ 1u, abort_flag)) {
+            atomicOr(P.err, kErrTimeoutEmpty);
+            *abort_flag = 1;
+            break;
+          }
+          const bool inner = p >= un.x0 && p < un.x1;
+          mbar_arrive_expect_tx(full, bytes_u + (inner ? bytes_in : 0u));
+          const uint32_t sb = smem_u32(smem + c.stage * P.stage_bytes);
+          tma_load_4d(sb, &d->tm_uh, un.z0 - R4, un.y0 - R, p, P.cur, full);
+          if (inner) {
+            tma_load_4d(sb + P.off_p, &d->tm_uc, un.z0, un.y0, p, P.prev, full);
+            tma_load_3d(sb + P.off_m, &d->tm_m, un.z0, un.y0, p, full);
+            if (GRAD) tma_load_4d(sb + P.off_f, &d->tm_f, un.z0, un.y0, p, P.fslot, full);
+            if (P.flags & kEtaField) tma_load_3d(sb + P.off_e, &d->tm_e, un.z0, un.y0, p, full);
+          }
+          ++issued;
+          c.next(S);
+        }
+      }
+      s_issued = issued;
+    }
+  } else {
+    // ------------------------------ consumers -----------------------------
+    const int ty0 = warp * NY;
+    Cursor ca{0, 0u};   // read-ahead cursor: every plane in order (centre values)
+    Cursor cb{0, 0u};   // compute cursor: the plane being updated
+    uint32_t tail_phase = 0u;
+    float q[NY][2 * R + 1];
+    const int tid = threadIdx.x;
+    bool ok = true;
+    for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
+      const Unit un = P.units[u];
+      const ShotDesc* d = P.shots + un.shot;
+      const int nx = d->nx, ny = d->ny, nz = d->nz, nzp = d->nzp;
+      const int mtype = d->mtype;
+      const bool etaf = (P.flags & kEtaField) != 0;
+      const int z = un.z0 + lane;
+      const bool zin = z < nz;
+      const float ez = (!etaf && zin) ? d->eta[nx + ny + z] : 0.f;
+      float ey[NY];
+#pragma unroll
+      for (int j = 0; j < NY; ++j) {
+        const int y = un.y0 + ty0 + j;
+        ey[j] = (!etaf && y < ny) ? d->eta[nx + y] : 0.f;
+      }
+      // warm-up: centre values of planes x0-R .. x0+R-1
+#pragma unroll
+      for (int i = 0; i < 2 * R; ++i) {
+        if (ok) ok = wait_or_abort(full0 + 8 * ca.stage, ca.phase, abort_flag);
+        const float* U = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes);
+#pragma unroll
+        for (int j = 0; j < NY; ++j) q[j][i] = ok ? U[(ty0 + j + R) * ZW + R4 + lane] : 0.f;
+        const int p = un.x0 - R + i;
+        if (p < un.x0 || p >= un.x1) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(empty0 + 8 * ca.stage);
+        }
+        ca.next(S);
+      }
+      if (!ok) break;
+      cb.skip(R, S);
+#pragma unroll 1
+      for (int x = un.x0; x < un.x1; ++x) {
+        // centre value of plane x+R joins the queue
+        if (!wait_or_abort(full0 + 8 * ca.stage, ca.phase, abort_flag)) { ok = false; break; }
+        {
+          const float* U = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes);
+#pragma unroll
+          for (int j = 0; j < NY; ++j) q[j][2 * R] = U[(ty0 + j + R) * ZW + R4 + lane];
+          if (x + R >= un.x1) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty0 + 8 * ca.stage);
+          }
+          ca.next(S);
+        }
+        // update plane x (its stage was waited for when its centre was read)
+        const unsigned char* sb = smem + cb.stage * P.stage_bytes;
+        const float* U = reinterpret_cast<const float*>(sb);
+        const float* Pp = reinterpret_cast<const float*>(sb + P.off_p);
+        const float ex = etaf ? 0.f : d->eta[x];
+        float* uo = d->u + (long long)P.out * d->uslot;
+#pragma unroll
+        for (int j = 0; j < NY; ++j) {
+          const int yl = ty0 + j;
+          const float c = q[j][R];
+          float lx = 0.f, ly = 0.f, lz = 0.f;
+          const float* row = U + (yl + R) * ZW + R4 + lane;
+#pragma unroll
+          for (int k = 1; k <= R; ++k) {
+            lx = fmaf(P.w[0][k], q[j][R - k] + q[j][R + k], lx);
+            ly = fmaf(P.w[1][k], row[-k * ZW] + row[k * ZW], ly);
+            lz = fmaf(P.w[2][k], row[-k] + row[k], lz);
+          }
+          const float lap = fmaf(P.csum, c, lx + ly + lz);
+          const int ci = yl * TZ + lane;
+          const float mv = smem_m(sb + P.off_m, mtype, ci);
+          const float e = etaf ? reinterpret_cast<const float*>(sb + P.off_e)[ci]
+                               : ex + ey[j] + ez;
+          const float prev = Pp[ci];
+          const float val = (2.f * mv * c - (mv - e) * prev + lap) / (mv + e);
+          const int y = un.y0 + yl;
+          if (zin && y < ny) {
+            const long long off = ((long long)x * ny + y) * nzp + z;
+            uo[off] = val;
+            if (GRAD) {
+              const float f = reinterpret_cast<const float*>(sb + P.off_f)[ci];
+              d->acc[off] = fmaf(f, val - 2.f * c + prev, d->acc[off]);
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty0 + 8 * cb.stage);
+        cb.next(S);
+#pragma unroll
+        for (int j = 0; j < NY; ++j)
+#pragma unroll
+          for (int i = 0; i < 2 * R; ++i) q[j][i] = q[j][i + 1];
+      }
+      if (!ok) break;
+      cb.skip(R, S);
+
+      // ---- unit tail: injection into u^{n+1} and sampling of u^n ----
+      mbar_arrive(tail);
+      if (!wait_or_abort(tail, tail_phase, abort_flag)) { ok = false; break; }
+      tail_phase ^= 1u;
+      if (P.flags & kInject) {
+        const int ib = P.inj_ptr[u], ie = P.inj_ptr[u + 1];
+        const float* A = d->inj_a + (long long)P.inj_row * d->inj_ld;
+        const float* B = (P.flags & kInjectDiff) ? d->inj_b + (long long)P.inj_row * d->inj_ld
+                                                 : nullptr;
+        float* uo = d->u + (long long)P.out * d->uslot;
+        for (int i = ib + tid; i < ie; i += NCONS) {
+          const InjNode nd = P.inj_nodes[i];
+          float s = 0.f;
+          for (int t = nd.tbeg; t < nd.tend; ++t) {
+            const InjTerm tm = P.inj_terms[t];
+            const float v = B ? A[tm.j] - B[tm.j] : A[tm.j];
+            s = fmaf(tm.w, v, s);
+          }
+          const long long off = ((long long)nd.x * ny + nd.y) * nzp + nd.z;
+          const float mv = load_m(d->m, mtype, off);
+          const float e = etaf ? d->etaf[off] : d->eta[nd.x] + d->eta[nx + nd.y] + d->eta[nx + ny + nd.z];
+          const float delta = P.dt2 * s / (mv + e);
+          uo[off] += delta;
+          if (GRAD) d->acc[off] = fmaf(d->fwd[(long long)P.fslot * d->fslot + off], delta, d->acc[off]);
+        }
+      }
+      if (P.flags & kSample) {
+        const int sbg = P.smp_ptr[u], se = P.smp_ptr[u + 1];
+        const float* uc = d->u + (long long)P.cur * d->uslot;
+        float* out = d->smp_out + (long long)P.smp_row * d->smp_ld;
+        for (int i = sbg + tid; i < se; i += NCONS) {
+          const int j = P.smp_pts[i];
+          const int bx = d->pt_base[3 * j], by = d->pt_base[3 * j + 1], bz = d->pt_base[3 * j + 2];
+          const float* w = d->pt_w + 8 * j;
+          float acc = 0.f;
+#pragma unroll
+          for (int cc = 0; cc < 8; ++cc) {
+            const float wc = w[cc];
+            if (wc != 0.f) {
+              const long long off =
+                  ((long long)(bx + ((cc >> 2) & 1)) * ny + (by + ((cc >> 1) & 1))) * nzp + bz + (cc & 1);
+              acc = fmaf(wc, uc[off], acc);
+            }
+          }
+          out[j] = acc;
+        }
+      }
+    }
+    if (!ok) {
+      atomicOr(P.err, kErrTimeoutFull);
+      *abort_flag = 1;
+    }
+  }
+  __syncthreads();
+  // On an aborted launch, wait (bounded) for the loads still in flight before
+  // the CTA's shared memory is released.
+  if (*abort_flag && threadIdx.x == BY * 32) {
+    const int issued = s_issued;
+    for (int k = (issued > S ? issued - S : 0); k < issued; ++k) {
+      const int st = k % S;
+      const uint32_t ph = (uint32_t)((k / S) & 1);
+      long long t0 = clock64();
+      while (!mbar_try_wait(full0 + 8 * st, ph) && clock64() - t0 < kWaitBudget) {
+      }
+    }
+  }
+}
+
+}  // namespace fdw

@@ -1,0 +1,17 @@
+// Step-kernel instantiations for stencil radius 5 (space order 10).
+#include "fdw_internal.h"
+#include "fdw_step.cuh"
+
+namespace fdw {
+
+const void* step_kernel_r5(int tile, bool grad) {
+  switch (tile) {
+    case 0: return grad ? (const void*)&step_kernel<5, 2, 8, true> : (const void*)&step_kernel<5, 2, 8, false>;
+    case 1: return grad ? (const void*)&step_kernel<5, 4, 8, true> : (const void*)&step_kernel<5, 4, 8, false>;
+    case 2: return grad ? (const void*)&step_kernel<5, 2, 4, true> : (const void*)&step_kernel<5, 2, 4, false>;
+    case 3: return grad ? (const void*)&step_kernel<5, 1, 1, true> : (const void*)&step_kernel<5, 1, 1, false>;
+    default: return nullptr;
+  }
+}
+
+}  // namespace fdw

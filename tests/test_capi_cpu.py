@@ -1,0 +1,88 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol that
+include/*.h declares, and its host-side logic (stencil weights, stability limit,
+argument validation) is correct.  No kernel is launched here."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fw():
+    from paper_1609_03361_gb300 import build, fdwave
+    build.build()
+    return fdwave
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"\b(fdw_[a-z0-9_]+)\s*\(", txt):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol(fw):
+    names = _declared()
+    assert len(names) >= 25
+    L = ctypes.CDLL(fw.LIB_PATH)
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+    # the binding declares exactly the header's functions
+    assert set(fw.declared_symbols()) == names
+
+
+def test_library_links_no_driver(fw):
+    # the CUDA driver is reached through the runtime's entry-point query only
+    out = os.popen(f"ldd {fw.LIB_PATH}").read()
+    assert "libcuda.so" not in out
+
+
+@pytest.mark.parametrize("p", range(2, 17, 2))
+def test_host_weights_match_oracle(fw, p):
+    # two independent implementations: Fornberg recursion (library) and the
+    # closed form (oracle)
+    a = fw.fdw_fd_weights(p)
+    b = oracle.fd_weights(p)
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("ndim,p,h,v", [(2, 4, 10.0, 1.5), (3, 8, 12.5, 2.625), (3, 16, 7.0, 4.5),
+                                        (3, 2, (10.0, 12.5, 5.0), 3.0)])
+def test_host_dt_max_matches_oracle(fw, ndim, p, h, v):
+    assert fw.fdw_dt_max(ndim, h, p, v) == pytest.approx(oracle.dt_max(ndim, h, p, v), rel=1e-12)
+
+
+def test_argument_validation_before_any_device_work(fw):
+    F = fw.FdwError
+    with pytest.raises(F) as e:
+        fw.fdw_create((10, 10, 10), 10.0, 7, 4, 1.0, 10, 2.0)
+    assert e.value.status == 3  # odd order
+    with pytest.raises(F) as e:
+        fw.fdw_create((10, 10, 10), 10.0, 18, 4, 1.0, 10, 2.0)
+    assert e.value.status == 3
+    with pytest.raises(F) as e:
+        fw.fdw_create((10, 1, 10), 10.0, 4, 4, 1.0, 10, 2.0)
+    assert e.value.status == 2  # dimension < 2
+    dtm = fw.fdw_dt_max(3, 10.0, 8, 2.0)
+    with pytest.raises(F) as e:
+        fw.fdw_create((10, 10, 10), 10.0, 8, 4, dtm * 1.001, 10, 2.0)
+    assert e.value.status == 4  # above the stability limit
+    assert fw.fdw_dt_max(3, 10.0, 5, 2.0) < 0
+    assert fw.fdw_dt_max(4, 10.0, 4, 2.0) < 0
+
+
+def test_status_strings(fw):
+    L = fw.lib()
+    for st in range(10):
+        assert L.fdw_status_string(st)
+    assert L.fdw_version() >= 100

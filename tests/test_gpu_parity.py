@@ -1,0 +1,258 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance: relative L2 <= 1e-4 for FP32 traces, wavefields and gradients
+(the accuracy target for the FP32 path); the FP32 adjoint identity to 1e-5.
+Sizes span several tiles in y and z with ragged tails and several x chunks.
+"""
+import numpy as np
+import pytest
+
+from problems import Problem, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def fw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_03361_gb300 import build, fdwave
+    build.build()
+    fdwave.lib()
+    return fdwave
+
+
+def _fwd(fw, pb, **kw):
+    s = pb.solver(fw, **kw)
+    rec = s.forward(pb.q32)
+    u = s.wavefield(0)
+    s.sync()
+    s.close()
+    return rec, u
+
+
+@pytest.mark.parametrize("p", [2, 4, 6, 8, 10, 12, 14, 16])
+def test_forward_3d_all_orders(fw, p):
+    pb = Problem((37, 45, 29), 10.0, p, 8, 70, nsrc=2, nrec=9, seed=p)
+    rec, u = _fwd(fw, pb)
+    ref, uref = pb.oracle_forward(final=True)
+    assert rel_l2(rec, ref) < TOL
+    assert rel_l2(u, uref) < TOL
+
+
+@pytest.mark.parametrize("tiling", [(0, 0, 0), (1, 0, 0), (2, 0, 0), (0, 5, 0), (0, 3, 6),
+                                    (1, 13, 0), (2, 64, 0), (0, 1, 0)])
+def test_forward_3d_tilings(fw, tiling):
+    pb = Problem((40, 51, 35), 12.5, 8, 6, 60, nsrc=3, nrec=12, seed=11)
+    rec, u = _fwd(fw, pb, tiling=tiling)
+    ref, uref = pb.oracle_forward(final=True)
+    assert rel_l2(rec, ref) < TOL
+    assert rel_l2(u, uref) < TOL
+
+
+def test_tilings_agree_bitwise(fw):
+    """Every tiling computes each point with the same arithmetic."""
+    pb = Problem((30, 33, 41), 10.0, 8, 5, 50, nsrc=2, nrec=8, seed=5)
+    base_rec, base_u = _fwd(fw, pb, tiling=(0, 0, 0))
+    for t in [(1, 0, 0), (2, 7, 0), (0, 2, 6), (1, 64, 9)]:
+        rec, u = _fwd(fw, pb, tiling=t)
+        assert np.array_equal(rec, base_rec), t
+        assert np.array_equal(u, base_u), t
+
+
+@pytest.mark.parametrize("p", [2, 4, 8, 16])
+def test_forward_2d(fw, p):
+    pb = Problem((61, 57), 10.0, p, 20, 200, nsrc=1, nrec=11, seed=3)
+    rec, u = _fwd(fw, pb)
+    ref, uref = pb.oracle_forward(final=True)
+    assert rel_l2(rec, ref) < TOL
+    assert rel_l2(u, uref) < TOL
+
+
+def test_forward_ongrid_and_edge_points(fw):
+    pb = Problem((25, 22, 27), 10.0, 4, 4, 60, nsrc=2, nrec=5, seed=8, ongrid=True)
+    top = np.array([(n - 1) * 10.0 for n in pb.shape])
+    pb.rec = np.vstack([pb.rec, top, np.zeros(3), [top[0], 0.0, 105.0], [55.0, 210.0, 260.0]])
+    rec, _ = _fwd(fw, pb)
+    ref = pb.oracle_forward()
+    assert rel_l2(rec, ref) < TOL
+
+
+@pytest.mark.parametrize("mtype", ["f16", "bf16"])
+def test_forward_low_precision_model(fw, mtype):
+    """The model stored in 16 bits: parity with the oracle run on the same
+    rounded model; the error against the FP32 model is recorded."""
+    pb = Problem((33, 30, 37), 12.5, 8, 6, 80, nsrc=1, nrec=8, seed=2)
+    rec, _ = _fwd(fw, pb, mtype=mtype)
+    mt = torch.float16 if mtype == "f16" else torch.bfloat16
+    m_rounded = torch.from_numpy(pb.m32).to(mt).to(torch.float32).numpy()
+    ref = pb.oracle_forward(m32=m_rounded)
+    assert rel_l2(rec, ref) < TOL
+    drift = rel_l2(rec, pb.oracle_forward())
+    assert drift < (2e-2 if mtype == "f16" else 1e-1)
+
+
+def test_device_and_host_arrays_agree(fw):
+    pb = Problem((26, 29, 31), 10.0, 6, 5, 50, nsrc=1, nrec=7, seed=4)
+    s = pb.solver(fw)
+    rec_h = s.forward(pb.q32)
+    rec_d = s.forward(torch.from_numpy(pb.q32).cuda()).cpu().numpy()
+    s.sync()
+    assert np.array_equal(rec_h, rec_d)
+    s.close()
+
+
+def test_degenerate_cases(fw):
+    # no sources: everything stays zero; no receivers: the call still runs
+    pb = Problem((20, 21, 22), 10.0, 4, 3, 30, nsrc=0, nrec=4, seed=1)
+    rec, u = _fwd(fw, pb)
+    assert np.count_nonzero(rec) == 0 and np.count_nonzero(u) == 0
+    pb = Problem((20, 21, 22), 10.0, 4, 3, 30, nsrc=1, nrec=0, seed=1)
+    s = pb.solver(fw)
+    s.forward(pb.q32, rec=np.zeros((30, 0), np.float32))
+    u = s.wavefield(0)
+    s.sync()
+    uref = pb.oracle_forward(final=True)[1]
+    assert rel_l2(u, uref) < TOL
+    # one time sample: u^0 = 0 is recorded
+    pb = Problem((20, 21, 22), 10.0, 4, 3, 1, nsrc=1, nrec=3, seed=1)
+    rec, _ = _fwd(fw, pb)
+    assert rec.shape == (1, 3) and np.count_nonzero(rec) == 0
+
+
+@pytest.mark.parametrize("ndim,p", [(3, 4), (3, 8), (3, 16), (2, 8)])
+def test_adjoint_parity_and_dot_test(fw, ndim, p):
+    shape = (31, 27, 35) if ndim == 3 else (50, 45)
+    pb = Problem(shape, 10.0, p, 6, 70, nsrc=2, nrec=7, seed=21 + p)
+    rng = np.random.default_rng(p)
+    d = rng.standard_normal((pb.nt, 7)).astype(np.float32)
+    s = pb.solver(fw)
+    qa = s.adjoint(d)
+    Fq = s.forward(pb.q32)
+    s.sync()
+    s.close()
+    ref = pb.oracle_adjoint(d)
+    assert rel_l2(qa, ref) < TOL
+    a = np.sum(Fq.astype(np.float64) * d)
+    b = np.sum(pb.q32.astype(np.float64) * qa)
+    assert abs(a - b) / abs(a) < 1e-5
+
+
+@pytest.mark.parametrize("k", [1, 4, 9, 70])
+def test_gradient_fp32_checkpoints(fw, k):
+    pb = Problem((29, 26, 31), 10.0, 8, 6, 70, nsrc=1, nrec=8, seed=31)
+    rng = np.random.default_rng(3)
+    resid = rng.standard_normal((pb.nt, 8)).astype(np.float32)
+    s = pb.solver(fw)
+    s.forward_ckpt(pb.q32, k, "f32")
+    g = s.gradient(resid)
+    s.sync()
+    s.close()
+    ref = pb.oracle_gradient(resid)
+    assert rel_l2(g, ref) < TOL
+
+
+@pytest.mark.parametrize("stype,tol", [("f16", 1e-2), ("bf16", 5e-2)])
+def test_gradient_low_precision_snapshots(fw, stype, tol):
+    pb = Problem((29, 26, 31), 10.0, 8, 6, 90, nsrc=1, nrec=8, seed=32)
+    resid = pb.oracle_forward().astype(np.float32)
+    s = pb.solver(fw)
+    s.forward_ckpt(pb.q32, 10, stype)
+    g = s.gradient(resid)
+    s.sync()
+    s.close()
+    ref = pb.oracle_gradient(resid)
+    assert rel_l2(g, ref) < tol
+
+
+def test_gradient_residual_difference_and_physical_layout(fw):
+    pb = Problem((24, 22, 26), 10.0, 4, 5, 60, nsrc=1, nrec=6, seed=41)
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((pb.nt, 6)).astype(np.float32)
+    b = rng.standard_normal((pb.nt, 6)).astype(np.float32)
+    s = pb.solver(fw)
+    s.forward_ckpt(pb.q32, 6, "f32")
+    g_phys = s.gradient(a, b, layout="physical")
+    g_comp = s.gradient(a - b, None, layout="computational")
+    s.sync()
+    s.close()
+    ref = pb.oracle_gradient(a.astype(np.float64) - b)
+    assert rel_l2(g_comp, ref) < TOL
+    # fold the oracle's layer gradient onto the physical edge cells
+    nbl = pb.nbl
+    fold = np.zeros(pb.shape)
+    n = ref.shape
+    for x in range(n[0]):
+        for y in range(n[1]):
+            cx = min(max(x - nbl, 0), pb.shape[0] - 1)
+            cy = min(max(y - nbl, 0), pb.shape[1] - 1)
+            cz = np.clip(np.arange(n[2]) - nbl, 0, pb.shape[2] - 1)
+            np.add.at(fold[cx, cy], cz, ref[x, y])
+    assert rel_l2(g_phys, fold) < TOL
+
+
+def test_batched_forward_matches_single(fw):
+    shapes = [(21, 24, 19), (30, 17, 26), (18, 18, 33)]
+    pbs = [Problem(sh, 12.5, 8, 5, 60, nsrc=1, nrec=5, seed=50 + i) for i, sh in enumerate(shapes)]
+    dt = min(pb.dt for pb in pbs)
+    vmax = max(pb.vmax for pb in pbs)
+    import oracle
+    for pb in pbs:
+        pb.dt = dt
+        pb.vmax = vmax
+        pb.setup = oracle.Setup(pb.shape, pb.h, pb.p, pb.nbl, dt, pb.nt)
+    solvers = [pb.solver(fw) for pb in pbs]
+    b = fw.Batch(solvers)
+    recs = b.forward([pb.q32 for pb in pbs])
+    for s in solvers:
+        s.sync()
+    for pb, rec in zip(pbs, recs):
+        assert rel_l2(rec, pb.oracle_forward()) < TOL
+        single = pb.solver(fw, tiling=(b.tiling()["tile"], b.tiling()["xchunk"], b.tiling()["stages"]))
+        r1 = single.forward(pb.q32)
+        single.sync()
+        assert np.array_equal(r1, rec)
+        single.close()
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+def test_batched_gradient_matches_oracle(fw):
+    shapes = [(21, 20, 19), (24, 17, 22)]
+    pbs = [Problem(sh, 12.5, 4, 5, 50, nsrc=1, nrec=5, seed=60 + i) for i, sh in enumerate(shapes)]
+    dt = min(pb.dt for pb in pbs)
+    vmax = max(pb.vmax for pb in pbs)
+    import oracle
+    for pb in pbs:
+        pb.dt = dt
+        pb.vmax = vmax
+        pb.setup = oracle.Setup(pb.shape, pb.h, pb.p, pb.nbl, dt, pb.nt)
+    solvers = [pb.solver(fw) for pb in pbs]
+    b = fw.Batch(solvers)
+    rng = np.random.default_rng(9)
+    res = [rng.standard_normal((pb.nt, 5)).astype(np.float32) for pb in pbs]
+    b.forward_ckpt([pb.q32 for pb in pbs], 7, "f32")
+    grads = b.gradient(res)
+    for s in solvers:
+        s.sync()
+    for pb, g, r in zip(pbs, grads, res):
+        assert rel_l2(g, pb.oracle_gradient(r)) < TOL
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+def test_autotune_keeps_results(fw):
+    pb = Problem((34, 30, 28), 10.0, 8, 6, 40, nsrc=1, nrec=6, seed=70)
+    s = pb.solver(fw)
+    s.autotune(3)
+    t = s.tiling()
+    assert t["tile"] in (0, 1, 2) and t["stages"] >= 6
+    rec = s.forward(pb.q32)
+    s.sync()
+    s.close()
+    assert rel_l2(rec, pb.oracle_forward()) < TOL
