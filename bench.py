@@ -1,0 +1,346 @@
+"""Benchmark of the GB300 acoustic finite-difference hot path.
+
+Default workload (one "step" = one complete forward modelling run): 3D acoustic
+forward on a 256^3 physical grid (336^3 computational with the 40-point layer),
+12.5 m spacing, space order 8, 1000 time samples (999 stencil updates per
+point), one off-grid 15 Hz Ricker source, 128 x 128 receivers at 20 m depth,
+FP32 arithmetic, FP32 model.  Inputs are synthetic (seeded two-layer model with
+a smoothed +-5% perturbation).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload forward|fwi|batched]
+
+Prints one JSON line (rank 0).  `value` is device-timed throughput in grid-point
+updates per second (GPts/s) with inputs resident in HBM; `e2e` is the same
+metric through the public API with pinned host buffers (model and wavelet
+copied in, traces copied out, every step).  Under torchrun each rank runs its
+own shot (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GPts/s & % HBM roofline (SO-8 3D FP32); FWI gradient s/shot, batched vs plain"
+B_ALG = 16  # algorithmic bytes per point update: read u^n, u^{n-1}, m; write u^{n+1}
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+KERNEL_SOURCES = ["paper_1609_03361_gb300/csrc/fdw_step.cuh",
+                  "paper_1609_03361_gb300/csrc/fdw_device.cuh",
+                  "paper_1609_03361_gb300/csrc/fdw_types.h"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- workloads
+
+def cfg2_workload(nt=1000):
+    from paper_1609_03361_gb300 import fdwave as fw
+    from paper_1609_03361_gb300 import workloads as W
+    w = W.config_3d(256, 12.5, 8, nt)
+    w.dt = W.choose_dt(fw.fdw_dt_max(3, 12.5, 8, w.vmax))
+    return w
+
+
+def cpu_baseline(w, target_s=15.0):
+    """FP64 oracle on the host cores: the full computational grid for a few
+    time steps, GPts/s (test infrastructure, timed as it stands)."""
+    import oracle
+    pts = int(np.prod(w.comp_shape))
+
+    def run(nts):
+        s = oracle.Setup(w.shape, w.spacing, w.space_order, w.nbl, w.dt, nts)
+        M = oracle.extend_model(s, w.m.astype(np.float32).astype(np.float64))
+        eta = oracle.damping(s, w.vmax)
+        q = w.wavelet()[:nts, None]
+        t = time.perf_counter()
+        oracle.forward(s, M, eta, w.src, q, w.rec)
+        return time.perf_counter() - t
+
+    t2 = run(2)  # one update: calibration
+    nts = int(max(2, min(200, target_s / max(t2, 1e-3)))) + 1
+    el = run(nts)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    if os.environ.get("OMP_NUM_THREADS"):
+        cores = min(cores, int(os.environ["OMP_NUM_THREADS"]))
+    return {"value": pts * (nts - 1) / el / 1e9, "unit": "GPts/s", "cores": cores, "kind": "oracle",
+            "sample": f"{w.comp_shape[0]}^3 computational grid, {nts - 1} FP64 time steps "
+                      f"({el:.1f} s), same model/source/receivers"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    w = cfg2_workload()
+    import oracle
+    pts = int(np.prod(w.comp_shape))
+    s2 = oracle.Setup(w.shape, w.spacing, w.space_order, w.nbl, w.dt, 2)
+    M = oracle.extend_model(s2, w.m.astype(np.float32).astype(np.float64))
+    eta = oracle.damping(s2, w.vmax)
+    q = w.wavelet()[:, None]
+
+    def sample(nts):
+        s = oracle.Setup(w.shape, w.spacing, w.space_order, w.nbl, w.dt, nts)
+        t = time.perf_counter()
+        oracle.forward(s, M, eta, w.src, q[:nts], w.rec)
+        return time.perf_counter() - t
+
+    t2 = sample(2)
+    per_step_budget = 150.0 / max(1, args.steps + args.warmup)
+    nts = int(max(2, min(50, per_step_budget / max(t2, 1e-3)))) + 1
+    for _ in range(args.warmup):
+        sample(2)
+    times = [sample(nts) for _ in range(args.steps)]
+    el = sum(times)
+    value = pts * (nts - 1) * args.steps / el / 1e9
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GPts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "3D acoustic forward 256^3 (336^3 computational), SO8, FP64 "
+                                   f"oracle sample of {nts - 1} time steps per step"},
+            "cpu_baseline": {"value": value, "unit": "GPts/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{nts - 1} time steps of the full 336^3 grid per step"},
+            "e2e": {"value": value, "unit": "GPts/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_forward(args, world, rank, local):
+    import torch
+    from paper_1609_03361_gb300 import fdwave as fw
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = cfg2_workload(args.nt)
+    pts = int(np.prod(w.comp_shape))
+    s = fw.Solver(w.shape, w.spacing, w.space_order, w.nbl, w.dt, w.nt, w.vmax, device=local)
+    m32 = w.m.astype(np.float32)
+    m_dev = torch.from_numpy(m32).to(dev)
+    s.set_model(m_dev)
+    s.set_sources(w.src)
+    s.set_receivers(w.rec)
+    q_dev = torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev)
+    rec_dev = torch.empty((w.nt, w.rec.shape[0]), dtype=torch.float32, device=dev)
+    if not args.no_autotune:
+        s.autotune(5)
+    tiling = s.tiling()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        s.forward(q_dev, rec_dev)
+    torch.cuda.synchronize(dev)
+    s.sync()
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.forward(q_dev, rec_dev)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    barrier(world)
+    ms_local = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms_local, world)
+    s.sync()
+    updates = pts * (w.nt - 1)
+    value = world * updates * args.steps / (ms * 1e-3) / 1e9
+    launches = args.steps * w.nt   # (nt-1) step kernels + 1 sampling kernel per forward
+
+    # roofline of the step kernel (its launches fill the timed region)
+    avg_launch_s = (ms_local * 1e-3) / (args.steps * (w.nt - 1))
+    achieved = B_ALG * pts / avg_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = None
+    try:
+        with open(PROFILE_TRAFFIC) as f:
+            tr = json.load(f)
+        if tr.get("kernel_hash") == kernel_hash() and tr.get("points") == pts:
+            traffic = tr["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "bytes_per_point": B_ALG, "points_per_launch": pts}
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        m_h = torch.from_numpy(m32).pin_memory()
+        q_h = torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).pin_memory()
+        rec_h = torch.empty((w.nt, w.rec.shape[0]), dtype=torch.float32).pin_memory()
+        s.set_model(m_h)
+        s.forward(q_h, rec_h)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s.set_model(m_h)
+            s.forward(q_h, rec_h)
+            torch.cuda.synchronize(dev)
+            float(rec_h[-1, 0])   # the host reads the result of the step
+        el = max_over_ranks(time.perf_counter() - t0, world)
+        assert torch.allclose(rec_h.to(dev), rec_dev), "host-buffer path disagrees"
+        e2e = {"value": world * updates * args.steps / el / 1e9, "unit": "GPts/s",
+               "h2d_bytes_per_step": int(m32.nbytes + q_h.numel() * 4),
+               "d2h_bytes_per_step": int(rec_h.numel() * 4)}
+    s.sync()
+
+    base = None
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        base = cpu_baseline(w)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GPts/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "3D acoustic forward, 256^3 physical (336^3 computational, "
+                                       "40-point layer), h=12.5 m, SO8, 1000 time samples, 1 "
+                                       "Ricker 15 Hz source, 128x128 receivers, FP32 model",
+                           "updates_per_step": updates, "parallelism": f"shots x{world}",
+                           "l2": "inputs larger than L2 (3 fields x 159 MB resident)",
+                           "tiling": tiling},
+                "roofline": roofline, "cpu_baseline": base, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    s.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="forward", choices=["forward"])
+    ap.add_argument("--nt", type=int, default=1000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "mine":
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    world, rank, local = dist_init()
+    run_forward(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -25,6 +25,8 @@
 //    during this step) and record the sampled points of u^n.
 #pragma once
 
+#include <cstdio>
+
 #include "fdw_device.cuh"
 
 namespace fdw {
@@ -47,6 +49,17 @@ struct Cursor {
   }
 };
 
+// Hand a pipeline stage back to the producer.  The consumer reads the stage
+// through the generic proxy while the producer refills it through the async
+// proxy (TMA); the mbarrier release/acquire chain alone does not order the two
+// proxies, so each lane fences its own reads before the warp arrives.  Without
+// the fence a read still in flight could observe the next plane's data.
+__device__ __forceinline__ void release_stage(uint32_t empty_bar, int lane) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) mbar_arrive(empty_bar);
+}
+
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort) {
 #pragma unroll 1
   for (int i = 0; i < 32; ++i)
@@ -59,6 +72,24 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
     if (clock64() - t0 > kWaitBudget) return false;
   }
 }
+
+#ifdef FDW_DEBUG_VERIFY
+// Debug builds only: compare a staged value with the global field it came from.
+__device__ int g_dbg_count;
+__device__ __forceinline__ void dbg_check(const char* what, float got, const float* base,
+                                          long long slot, int x, int y, int z, int nx, int ny,
+                                          int nz, int nzp, int u, int warp, int extra) {
+  float want = 0.f;
+  if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz)
+    want = base[slot + ((long long)x * ny + y) * nzp + z];
+  if (got != want) {
+    const int k = atomicAdd(&g_dbg_count, 1);
+    if (k < 24)
+      printf("DBG %s unit %d warp %d x %d y %d z %d got %g want %g extra %d blk %d\n", what, u,
+             warp, x, y, z, got, want, extra, blockIdx.x);
+  }
+}
+#endif
 
 template <int R, int NY, int BY, bool GRAD>
 __global__ void __launch_bounds__((BY + 1) * 32)
@@ -163,10 +194,12 @@ step_kernel(const __grid_constant__ StepParams P) {
 #pragma unroll
         for (int j = 0; j < NY; ++j) q[j][i] = ok ? U[(ty0 + j + R) * ZW + R4 + lane] : 0.f;
         const int p = un.x0 - R + i;
-        if (p < un.x0 || p >= un.x1) {
-          __syncwarp();
-          if (lane == 0) mbar_arrive(empty0 + 8 * ca.stage);
-        }
+#ifdef FDW_DEBUG_VERIFY
+        for (int j = 0; j < NY; ++j)
+          dbg_check("warm", q[j][i], d->u, (long long)P.cur * d->uslot, p, un.y0 + ty0 + j, z, nx,
+                    ny, nz, nzp, u, warp, i);
+#endif
+        if (p < un.x0 || p >= un.x1) release_stage(empty0 + 8 * ca.stage, lane);
         ca.next(S);
       }
       if (!ok) break;
@@ -179,12 +212,16 @@ step_kernel(const __grid_constant__ StepParams P) {
           const float* U = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes);
 #pragma unroll
           for (int j = 0; j < NY; ++j) q[j][2 * R] = U[(ty0 + j + R) * ZW + R4 + lane];
-          if (x + R >= un.x1) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(empty0 + 8 * ca.stage);
-          }
-          ca.next(S);
+#ifdef FDW_DEBUG_VERIFY
+          for (int j = 0; j < NY; ++j)
+            dbg_check("ahead", q[j][2 * R], d->u, (long long)P.cur * d->uslot, x + R,
+                      un.y0 + ty0 + j, z, nx, ny, nz, nzp, u, warp, x - un.x0);
+#endif
         }
+        // a look-ahead plane past the chunk is only needed for its centre
+        // value; it is handed back after the update below has consumed it
+        const int ahead_stage = ca.stage;
+        ca.next(S);
         // update plane x (its stage was waited for when its centre was read)
         const unsigned char* sb = smem + cb.stage * P.stage_bytes;
         const float* U = reinterpret_cast<const float*>(sb);
@@ -209,6 +246,19 @@ step_kernel(const __grid_constant__ StepParams P) {
           const float e = etaf ? reinterpret_cast<const float*>(sb + P.off_e)[ci]
                                : ex + ey[j] + ez;
           const float prev = Pp[ci];
+#ifdef FDW_DEBUG_VERIFY
+          for (int k = -R; k <= R; ++k) {
+            dbg_check("xq", q[j][R + k], d->u, (long long)P.cur * d->uslot, x + k, un.y0 + yl, z,
+                      nx, ny, nz, nzp, u, warp, k);
+            dbg_check("yn", row[k * ZW], d->u, (long long)P.cur * d->uslot, x, un.y0 + yl + k, z,
+                      nx, ny, nz, nzp, u, warp, k);
+            dbg_check("zn", row[k], d->u, (long long)P.cur * d->uslot, x, un.y0 + yl, z + k, nx,
+                      ny, nz, nzp, u, warp, k);
+          }
+          if (un.y0 + yl < ny && zin)
+            dbg_check("prev", prev, d->u, (long long)P.prev * d->uslot, x, un.y0 + yl, z, nx, ny,
+                      nz, nzp, u, warp, 0);
+#endif
           const float val = (2.f * mv * c - (mv - e) * prev + lap) / (mv + e);
           const int y = un.y0 + yl;
           if (zin && y < ny) {
@@ -220,8 +270,8 @@ step_kernel(const __grid_constant__ StepParams P) {
             }
           }
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty0 + 8 * cb.stage);
+        release_stage(empty0 + 8 * cb.stage, lane);
+        if (x + R >= un.x1) release_stage(empty0 + 8 * ahead_stage, lane);
         cb.next(S);
 #pragma unroll
         for (int j = 0; j < NY; ++j)

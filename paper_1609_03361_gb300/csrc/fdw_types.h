@@ -27,8 +27,8 @@ enum StepFlags : int {
   kInjectDiff = 8,   // inject (a - b) instead of a
 };
 
-// Per-shot description; lives in device memory, 64-byte aligned (tensor maps).
-struct alignas(64) ShotDesc {
+// Per-shot description; lives in device memory, 128-byte aligned (tensor maps).
+struct alignas(128) ShotDesc {
   CUtensorMap tm_uh;   // wavefield slots [slots][nx][ny][nzp] f32, halo box (TZ+2R4, TY+2R, 1, 1)
   CUtensorMap tm_uc;   // the same slots, centre box (TZ, TY, 1, 1)
   CUtensorMap tm_m;    // model [nx][ny][nzp] (f32 / f16 / bf16), centre box (TZ, TY, 1)

@@ -19,7 +19,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfdwave.so")
+LIB_PATH = os.environ.get("FDW_LIB_PATH") or os.path.join(_HERE, "libfdwave.so")
 
 FDW_OK = 0
 FDW_F32, FDW_F16, FDW_BF16 = 0, 1, 2
