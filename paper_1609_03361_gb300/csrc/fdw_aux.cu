@@ -1,6 +1,6 @@
 // Auxiliary kernels of libfdwave: per-call work around the time loop.
 //  - sampling of the last time level (grid-to-point, Sec. 5.2),
-//  - model set-up (edge extension into the layer, storage-type conversion),
+//  - model set-up (edge extension into the layer, s = 1/m, storage-type conversion),
 //  - damping-field set-up,
 //  - checkpoint snapshots: absolute maximum, pack to 16 bits with a scale,
 //    unpack,
@@ -73,9 +73,10 @@ __global__ void model_kernel(const float* in, int layout, int px, int py, int pz
       v = in[i];
     }
     const long long o = pitched(g, i);
-    if (mtype == kF16) static_cast<__half*>(out)[o] = __float2half_rn(v);
-    else if (mtype == kBF16) static_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(v);
-    else static_cast<float*>(out)[o] = v;
+    const float sv = 1.0f / v;  // stored as s = 1/m (squared velocity)
+    if (mtype == kF16) static_cast<__half*>(out)[o] = __float2half_rn(sv);
+    else if (mtype == kBF16) static_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(sv);
+    else static_cast<float*>(out)[o] = sv;
   }
 }
 

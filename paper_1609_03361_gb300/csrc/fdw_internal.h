@@ -7,14 +7,16 @@
 
 namespace fdw {
 
-// Tile shapes of the step kernel: NY points along y per consumer thread and BY
-// consumer warps, so a tile is (BY * NY) x 32 points in (y, z).
+// Tile shapes of the step kernel: BY consumer warps; each half-warp covers NY
+// consecutive rows and each lane two z points, so a tile is (2 * BY * NY) x 32
+// points in (y, z).
 struct TileShape {
   int ny_pts;
   int warps;
 };
 constexpr int kNumTiles = 4;
-constexpr TileShape kTiles[kNumTiles] = {{2, 8}, {4, 8}, {2, 4}, {1, 1}};
+constexpr TileShape kTiles[kNumTiles] = {{1, 8}, {2, 8}, {2, 4}, {1, 1}};
+constexpr int tile_rows(const TileShape& t) { return 2 * t.ny_pts * t.warps; }
 
 // Kernel registry: one translation unit per stencil radius.
 const void* step_kernel_r1(int tile, bool grad);

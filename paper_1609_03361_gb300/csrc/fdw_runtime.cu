@@ -440,8 +440,7 @@ struct StageLayout {
 static int round128(int x) { return (x + 127) & ~127; }
 
 static StageLayout stage_layout(int r, int tile, int mt_bytes, bool grad, bool etaf) {
-  const TileShape t = kTiles[tile];
-  const int TY = t.ny_pts * t.warps;
+  const int TY = tile_rows(kTiles[tile]);
   const int R4 = (r + 3) & ~3;
   const int ZW = kTZ + 2 * R4, YW = TY + 2 * r;
   StageLayout L;
@@ -507,7 +506,7 @@ static void choose_default_tiling(Plan& pl) {
   }
   // aim at >= 4 units per resident CTA so the static schedule balances
   const int slots = resident_ctas(pl, pl.tile, pl.stages, false);
-  const int TY = kTiles[pl.tile].ny_pts * kTiles[pl.tile].warps;
+  const int TY = tile_rows(kTiles[pl.tile]);
   long long cols = 0;
   int nxmax = 1;
   for (auto* c : pl.shots) {
@@ -529,8 +528,7 @@ static void upload_vec(void** dptr, const void* src, size_t bytes) {
 static void build_lists(Plan& pl) {
   pl.release_lists();
   pl.clear_graphs();
-  const TileShape t = kTiles[pl.tile];
-  const int TY = t.ny_pts * t.warps;
+  const int TY = tile_rows(kTiles[pl.tile]);
   pl.units.clear();
   std::vector<int> shot_first(pl.shots.size() + 1, 0);
   std::vector<std::array<int, 3>> counts(pl.shots.size());
@@ -621,8 +619,7 @@ static void build_lists(Plan& pl) {
 static ShotDesc make_desc(const Plan& pl, fdw_ctx* c, int role) {
   ShotDesc d;
   std::memset(&d, 0, sizeof(d));
-  const TileShape t = kTiles[pl.tile];
-  const int TY = t.ny_pts * t.warps;
+  const int TY = tile_rows(kTiles[pl.tile]);
   const int R4 = (pl.r + 3) & ~3;
   float* ubuf = nullptr;
   int uslots = 2;

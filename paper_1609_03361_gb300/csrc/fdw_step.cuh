@@ -11,15 +11,19 @@
 // accumulates the FWI imaging term u^k (lambda^k - 2 lambda^{k+1} + lambda^{k+2}).
 //
 // Layout: every field is [x][y][zp] (z contiguous, rows padded to zp), x the
-// slowest axis.  A CTA owns a column tile of TY x TZ points (y, z) and streams
-// along a chunk [x0, x1) of x:
+// slowest axis.  The model is stored as s = 1/m, so the update reads
+//     u^{n+1} = [ 2 u^n - (1 - e s) u^{n-1} + s dt^2 L u^n ] / (1 + e s),  e = eta dt/2,
+// which needs no division where e = 0.  A CTA owns a column tile of TY x TZ
+// points (y, z) and streams along a chunk [x0, x1) of x:
 //  - a producer warp issues TMA loads, one pipeline stage per x plane: the
 //    u^n plane with its (r, R4) halo in y and z (zero-filled outside the grid,
 //    which is the zero halo of the scheme), and for computed planes the
 //    u^{n-1}, m (and forward-wavefield / damping) tiles;
 //  - consumer warps keep the 2r+1 values of u^n along x of their points in
-//    registers (a sliding queue), take y and z neighbours from shared memory,
-//    write u^{n+1} with coalesced stores and release the stage;
+//    registers (a queue whose slots rotate: the x loop is unrolled by 2r+1),
+//    take y and z neighbours from shared memory with 8-byte loads (each lane
+//    owns two z-neighbouring points, each half-warp NY rows), write u^{n+1}
+//    with 8-byte coalesced stores and release the stage;
 //  - after the chunk, the consumers add the injected values into the nodes the
 //    unit owns (deterministic order, no atomics: no other CTA reads u^{n+1}
 //    during this step) and record the sampled points of u^n.
@@ -73,29 +77,217 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
   }
 }
 
+
+// Model values are stored as s = 1/m (squared velocity) in one of three types.
+template <typename MT>
+__device__ __forceinline__ float2 load_pair(const unsigned char* base, int i);
+template <>
+__device__ __forceinline__ float2 load_pair<float>(const unsigned char* base, int i) {
+  return *reinterpret_cast<const float2*>(base + 4 * i);
+}
+template <>
+__device__ __forceinline__ float2 load_pair<__half>(const unsigned char* base, int i) {
+  return __half22float2(*reinterpret_cast<const __half2*>(base + 2 * i));
+}
+template <>
+__device__ __forceinline__ float2 load_pair<__nv_bfloat16>(const unsigned char* base, int i) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(base + 2 * i));
+}
+
+__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ float pick(const float2& a, int v) { return v ? a.y : a.x; }
+
+// Thread layout of a consumer warp: two half-warps, each on NY consecutive
+// rows (y) of the tile; every lane owns two neighbouring points along z.
+template <int NY>
+struct Lanes {
+  int r0;  // first local row of the thread
+  int zl;  // local z of the thread's first point (even)
+};
+
 #ifdef FDW_DEBUG_VERIFY
 // Debug builds only: compare a staged value with the global field it came from.
 __device__ int g_dbg_count;
 __device__ __forceinline__ void dbg_check(const char* what, float got, const float* base,
                                           long long slot, int x, int y, int z, int nx, int ny,
-                                          int nz, int nzp, int u, int warp, int extra) {
+                                          int nz, int nzp, int u) {
   float want = 0.f;
   if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz)
     want = base[slot + ((long long)x * ny + y) * nzp + z];
   if (got != want) {
     const int k = atomicAdd(&g_dbg_count, 1);
     if (k < 24)
-      printf("DBG %s unit %d warp %d x %d y %d z %d got %g want %g extra %d blk %d\n", what, u,
-             warp, x, y, z, got, want, extra, blockIdx.x);
+      printf("DBG %s unit %d x %d y %d z %d got %g want %g blk %d\n", what, u, x, y, z, got, want,
+             blockIdx.x);
   }
 }
 #endif
+
+// Streams one work unit through the pipeline: warm-up of the x queue, then
+// one update per plane of [x0, x1).  Returns false if a wait gave up.
+template <int R, int NY, int BY, bool GRAD, typename MT>
+__device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, const ShotDesc* d,
+                                         int u, const unsigned char* smem, uint32_t full0,
+                                         uint32_t empty0, Cursor& ca, Cursor& cb,
+                                         volatile int* abort_flag, int lane, const Lanes<NY> L) {
+  constexpr int TZ = kTZ;
+  constexpr int R4 = Halo<R>::R4;
+  constexpr int ZW = Halo<R>::ZW;
+  constexpr int Q = 2 * R + 1;  // x queue length; the x loop is unrolled by Q
+  const int S = P.stages;
+  const int nx = d->nx, ny = d->ny, nz = d->nz, nzp = d->nzp;
+  const bool etaf = (P.flags & kEtaField) != 0;
+  const int r0 = L.r0, zl = L.zl;
+  const int z = un.z0 + zl;
+  const bool zin = z < nz;
+  (void)nx;
+
+  // damping: y and z parts of the separable profile, per point
+  float eyz[NY][2];
+  int rowoff[NY];
+  bool rowok[NY];
+#pragma unroll
+  for (int j = 0; j < NY; ++j) {
+    const int y = un.y0 + r0 + j;
+    const float ey = (!etaf && y < ny) ? d->eta[d->nx + y] : 0.f;
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int zz = z + v;
+      eyz[j][v] = ey + ((!etaf && zz < nz) ? d->eta[d->nx + ny + zz] : 0.f);
+    }
+    rowok[j] = zin && y < ny;
+    rowoff[j] = y * nzp + z;
+  }
+  const long long plane = (long long)ny * nzp;
+
+  // x queue of centre values: slot (p - x0 + R) mod Q holds plane p
+  float qv[NY][2][Q];
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < 2 * R; ++i) {
+    if (ok) ok = wait_or_abort(full0 + 8 * ca.stage, ca.phase, abort_flag);
+    const float* U = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes);
+#pragma unroll
+    for (int j = 0; j < NY; ++j) {
+      const float2 cv = ok ? lds2(U + (r0 + j + R) * ZW + R4 + zl) : make_float2(0.f, 0.f);
+      qv[j][0][i] = cv.x;
+      qv[j][1][i] = cv.y;
+#ifdef FDW_DEBUG_VERIFY
+      dbg_check("warm", cv.x, d->u, (long long)P.cur * d->uslot, un.x0 - R + i, un.y0 + r0 + j,
+                z, d->nx, ny, nz, nzp, u);
+#endif
+    }
+    const int p = un.x0 - R + i;
+    if (p < un.x0 || p >= un.x1) release_stage(empty0 + 8 * ca.stage, lane);
+    ca.next(S);
+  }
+  if (!ok) return false;
+  cb.skip(R, S);
+
+  float* uo = d->u + (long long)P.out * d->uslot;
+  float* acc = d->acc;
+#pragma unroll 1
+  for (int xb = un.x0; xb < un.x1; xb += Q) {
+#pragma unroll
+    for (int t = 0; t < Q; ++t) {
+      const int x = xb + t;
+      if (x >= un.x1) break;
+      // centre values of plane x+R join the queue
+      if (!wait_or_abort(full0 + 8 * ca.stage, ca.phase, abort_flag)) return false;
+      {
+        const float* Ua = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes);
+#pragma unroll
+        for (int j = 0; j < NY; ++j) {
+          const float2 cv = lds2(Ua + (r0 + j + R) * ZW + R4 + zl);
+          qv[j][0][(t + 2 * R) % Q] = cv.x;
+          qv[j][1][(t + 2 * R) % Q] = cv.y;
+#ifdef FDW_DEBUG_VERIFY
+          dbg_check("ahead", cv.x, d->u, (long long)P.cur * d->uslot, x + R, un.y0 + r0 + j, z,
+                    d->nx, ny, nz, nzp, u);
+#endif
+        }
+      }
+      const int ahead_stage = ca.stage;
+      ca.next(S);
+
+      // neighbours in y and z of plane x from the staged halo plane
+      const unsigned char* sb = smem + cb.stage * P.stage_bytes;
+      const float* U = reinterpret_cast<const float*>(sb);
+      float2 yr[NY + 2 * R];
+      float wz[NY][2 + 2 * R4];
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        yr[i] = lds2(U + (r0 + i) * ZW + R4 + zl);
+        yr[NY + R + i] = lds2(U + (r0 + NY + R + i) * ZW + R4 + zl);
+      }
+#pragma unroll
+      for (int j = 0; j < NY; ++j) {
+#pragma unroll
+        for (int i = 0; i <= R4; ++i) {
+          const float2 w2 = lds2(U + (r0 + j + R) * ZW + zl + 2 * i);
+          wz[j][2 * i] = w2.x;
+          wz[j][2 * i + 1] = w2.y;
+        }
+        yr[R + j] = make_float2(wz[j][R4], wz[j][R4 + 1]);
+      }
+      const float ex = etaf ? 0.f : d->eta[x];
+      const float* Pp = reinterpret_cast<const float*>(sb + P.off_p);
+      const long long xoff = (long long)x * plane;
+#pragma unroll
+      for (int j = 0; j < NY; ++j) {
+        const int li = (r0 + j) * TZ + zl;
+        const float2 pv = lds2(Pp + li);
+        const float2 sv = load_pair<MT>(sb + P.off_m, li);
+        float2 ev;
+        if (etaf) ev = lds2(reinterpret_cast<const float*>(sb + P.off_e) + li);
+        else ev = make_float2(ex + eyz[j][0], ex + eyz[j][1]);
+        float val[2], cc[2];
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const float c = wz[j][R4 + v];
+          float lx = 0.f, ly = 0.f, lz = 0.f;
+#pragma unroll
+          for (int k = 1; k <= R; ++k) {
+            lx = fmaf(P.w[0][k], qv[j][v][(t + R - k) % Q] + qv[j][v][(t + R + k) % Q], lx);
+            ly = fmaf(P.w[1][k], pick(yr[R + j - k], v) + pick(yr[R + j + k], v), ly);
+            lz = fmaf(P.w[2][k], wz[j][R4 + v - k] + wz[j][R4 + v + k], lz);
+          }
+          const float lap = fmaf(P.csum, c, lx + ly + lz);
+          const float s = pick(sv, v), e = pick(ev, v), prev = pick(pv, v);
+          const float es = e * s;
+          // [2u - (1 - e s) u- + s dt^2 L u] / (1 + e s): the three-level update divided by m
+          const float num = fmaf(es, prev, fmaf(s, lap, 2.f * c) - prev);
+          val[v] = __fdividef(num, 1.f + es);
+          cc[v] = c;
+        }
+        if (rowok[j]) {
+          const long long off = xoff + rowoff[j];
+          *reinterpret_cast<float2*>(uo + off) = make_float2(val[0], val[1]);
+          if (GRAD) {
+            const float2 f = lds2(reinterpret_cast<const float*>(sb + P.off_f) + li);
+            float2 a = *reinterpret_cast<const float2*>(acc + off);
+            a.x = fmaf(f.x, val[0] - 2.f * cc[0] + pv.x, a.x);
+            a.y = fmaf(f.y, val[1] - 2.f * cc[1] + pv.y, a.y);
+            *reinterpret_cast<float2*>(acc + off) = a;
+          }
+        }
+      }
+      release_stage(empty0 + 8 * cb.stage, lane);
+      // a look-ahead plane past the chunk is only needed for its centre
+      // value; it is handed back after the update has consumed it
+      if (x + R >= un.x1) release_stage(empty0 + 8 * ahead_stage, lane);
+      cb.next(S);
+    }
+  }
+  cb.skip(R, S);
+  return true;
+}
 
 template <int R, int NY, int BY, bool GRAD>
 __global__ void __launch_bounds__((BY + 1) * 32)
 step_kernel(const __grid_constant__ StepParams P) {
   constexpr int TZ = kTZ;
-  constexpr int TY = BY * NY;
+  constexpr int TY = 2 * BY * NY;
   constexpr int R4 = Halo<R>::R4;
   constexpr int ZW = Halo<R>::ZW;
   constexpr int YW = TY + 2 * R;
@@ -164,127 +356,35 @@ step_kernel(const __grid_constant__ StepParams P) {
     }
   } else {
     // ------------------------------ consumers -----------------------------
-    const int ty0 = warp * NY;
+    Lanes<NY> L;
+    L.r0 = warp * 2 * NY + (lane >> 4) * NY;
+    L.zl = 2 * (lane & 15);
     Cursor ca{0, 0u};   // read-ahead cursor: every plane in order (centre values)
     Cursor cb{0, 0u};   // compute cursor: the plane being updated
     uint32_t tail_phase = 0u;
-    float q[NY][2 * R + 1];
     const int tid = threadIdx.x;
     bool ok = true;
     for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
       const Unit un = P.units[u];
       const ShotDesc* d = P.shots + un.shot;
-      const int nx = d->nx, ny = d->ny, nz = d->nz, nzp = d->nzp;
       const int mtype = d->mtype;
-      const bool etaf = (P.flags & kEtaField) != 0;
-      const int z = un.z0 + lane;
-      const bool zin = z < nz;
-      const float ez = (!etaf && zin) ? d->eta[nx + ny + z] : 0.f;
-      float ey[NY];
-#pragma unroll
-      for (int j = 0; j < NY; ++j) {
-        const int y = un.y0 + ty0 + j;
-        ey[j] = (!etaf && y < ny) ? d->eta[nx + y] : 0.f;
-      }
-      // warm-up: centre values of planes x0-R .. x0+R-1
-#pragma unroll
-      for (int i = 0; i < 2 * R; ++i) {
-        if (ok) ok = wait_or_abort(full0 + 8 * ca.stage, ca.phase, abort_flag);
-        const float* U = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes);
-#pragma unroll
-        for (int j = 0; j < NY; ++j) q[j][i] = ok ? U[(ty0 + j + R) * ZW + R4 + lane] : 0.f;
-        const int p = un.x0 - R + i;
-#ifdef FDW_DEBUG_VERIFY
-        for (int j = 0; j < NY; ++j)
-          dbg_check("warm", q[j][i], d->u, (long long)P.cur * d->uslot, p, un.y0 + ty0 + j, z, nx,
-                    ny, nz, nzp, u, warp, i);
-#endif
-        if (p < un.x0 || p >= un.x1) release_stage(empty0 + 8 * ca.stage, lane);
-        ca.next(S);
-      }
+      if (mtype == kF16)
+        ok = run_unit<R, NY, BY, GRAD, __half>(P, un, d, u, smem, full0, empty0, ca, cb,
+                                               abort_flag, lane, L);
+      else if (mtype == kBF16)
+        ok = run_unit<R, NY, BY, GRAD, __nv_bfloat16>(P, un, d, u, smem, full0, empty0, ca, cb,
+                                                      abort_flag, lane, L);
+      else
+        ok = run_unit<R, NY, BY, GRAD, float>(P, un, d, u, smem, full0, empty0, ca, cb,
+                                              abort_flag, lane, L);
       if (!ok) break;
-      cb.skip(R, S);
-#pragma unroll 1
-      for (int x = un.x0; x < un.x1; ++x) {
-        // centre value of plane x+R joins the queue
-        if (!wait_or_abort(full0 + 8 * ca.stage, ca.phase, abort_flag)) { ok = false; break; }
-        {
-          const float* U = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes);
-#pragma unroll
-          for (int j = 0; j < NY; ++j) q[j][2 * R] = U[(ty0 + j + R) * ZW + R4 + lane];
-#ifdef FDW_DEBUG_VERIFY
-          for (int j = 0; j < NY; ++j)
-            dbg_check("ahead", q[j][2 * R], d->u, (long long)P.cur * d->uslot, x + R,
-                      un.y0 + ty0 + j, z, nx, ny, nz, nzp, u, warp, x - un.x0);
-#endif
-        }
-        // a look-ahead plane past the chunk is only needed for its centre
-        // value; it is handed back after the update below has consumed it
-        const int ahead_stage = ca.stage;
-        ca.next(S);
-        // update plane x (its stage was waited for when its centre was read)
-        const unsigned char* sb = smem + cb.stage * P.stage_bytes;
-        const float* U = reinterpret_cast<const float*>(sb);
-        const float* Pp = reinterpret_cast<const float*>(sb + P.off_p);
-        const float ex = etaf ? 0.f : d->eta[x];
-        float* uo = d->u + (long long)P.out * d->uslot;
-#pragma unroll
-        for (int j = 0; j < NY; ++j) {
-          const int yl = ty0 + j;
-          const float c = q[j][R];
-          float lx = 0.f, ly = 0.f, lz = 0.f;
-          const float* row = U + (yl + R) * ZW + R4 + lane;
-#pragma unroll
-          for (int k = 1; k <= R; ++k) {
-            lx = fmaf(P.w[0][k], q[j][R - k] + q[j][R + k], lx);
-            ly = fmaf(P.w[1][k], row[-k * ZW] + row[k * ZW], ly);
-            lz = fmaf(P.w[2][k], row[-k] + row[k], lz);
-          }
-          const float lap = fmaf(P.csum, c, lx + ly + lz);
-          const int ci = yl * TZ + lane;
-          const float mv = smem_m(sb + P.off_m, mtype, ci);
-          const float e = etaf ? reinterpret_cast<const float*>(sb + P.off_e)[ci]
-                               : ex + ey[j] + ez;
-          const float prev = Pp[ci];
-#ifdef FDW_DEBUG_VERIFY
-          for (int k = -R; k <= R; ++k) {
-            dbg_check("xq", q[j][R + k], d->u, (long long)P.cur * d->uslot, x + k, un.y0 + yl, z,
-                      nx, ny, nz, nzp, u, warp, k);
-            dbg_check("yn", row[k * ZW], d->u, (long long)P.cur * d->uslot, x, un.y0 + yl + k, z,
-                      nx, ny, nz, nzp, u, warp, k);
-            dbg_check("zn", row[k], d->u, (long long)P.cur * d->uslot, x, un.y0 + yl, z + k, nx,
-                      ny, nz, nzp, u, warp, k);
-          }
-          if (un.y0 + yl < ny && zin)
-            dbg_check("prev", prev, d->u, (long long)P.prev * d->uslot, x, un.y0 + yl, z, nx, ny,
-                      nz, nzp, u, warp, 0);
-#endif
-          const float val = (2.f * mv * c - (mv - e) * prev + lap) / (mv + e);
-          const int y = un.y0 + yl;
-          if (zin && y < ny) {
-            const long long off = ((long long)x * ny + y) * nzp + z;
-            uo[off] = val;
-            if (GRAD) {
-              const float f = reinterpret_cast<const float*>(sb + P.off_f)[ci];
-              d->acc[off] = fmaf(f, val - 2.f * c + prev, d->acc[off]);
-            }
-          }
-        }
-        release_stage(empty0 + 8 * cb.stage, lane);
-        if (x + R >= un.x1) release_stage(empty0 + 8 * ahead_stage, lane);
-        cb.next(S);
-#pragma unroll
-        for (int j = 0; j < NY; ++j)
-#pragma unroll
-          for (int i = 0; i < 2 * R; ++i) q[j][i] = q[j][i + 1];
-      }
-      if (!ok) break;
-      cb.skip(R, S);
 
       // ---- unit tail: injection into u^{n+1} and sampling of u^n ----
       mbar_arrive(tail);
       if (!wait_or_abort(tail, tail_phase, abort_flag)) { ok = false; break; }
       tail_phase ^= 1u;
+      const int nx = d->nx, ny = d->ny, nzp = d->nzp;
+      const bool etaf = (P.flags & kEtaField) != 0;
       if (P.flags & kInject) {
         const int ib = P.inj_ptr[u], ie = P.inj_ptr[u + 1];
         const float* A = d->inj_a + (long long)P.inj_row * d->inj_ld;
@@ -293,16 +393,18 @@ step_kernel(const __grid_constant__ StepParams P) {
         float* uo = d->u + (long long)P.out * d->uslot;
         for (int i = ib + tid; i < ie; i += NCONS) {
           const InjNode nd = P.inj_nodes[i];
-          float s = 0.f;
+          float sum = 0.f;
           for (int t = nd.tbeg; t < nd.tend; ++t) {
             const InjTerm tm = P.inj_terms[t];
             const float v = B ? A[tm.j] - B[tm.j] : A[tm.j];
-            s = fmaf(tm.w, v, s);
+            sum = fmaf(tm.w, v, sum);
           }
           const long long off = ((long long)nd.x * ny + nd.y) * nzp + nd.z;
-          const float mv = load_m(d->m, mtype, off);
-          const float e = etaf ? d->etaf[off] : d->eta[nd.x] + d->eta[nx + nd.y] + d->eta[nx + ny + nd.z];
-          const float delta = P.dt2 * s / (mv + e);
+          const float s = load_m(d->m, mtype, off);
+          const float e = etaf ? d->etaf[off]
+                               : d->eta[nd.x] + d->eta[nx + nd.y] + d->eta[nx + ny + nd.z];
+          // dt^2 q / (m + eta dt/2) with s = 1/m
+          const float delta = P.dt2 * sum * s / (1.f + e * s);
           uo[off] += delta;
           if (GRAD) d->acc[off] = fmaf(d->fwd[(long long)P.fslot * d->fslot + off], delta, d->acc[off]);
         }

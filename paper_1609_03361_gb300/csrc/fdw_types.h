@@ -31,7 +31,7 @@ enum StepFlags : int {
 struct alignas(128) ShotDesc {
   CUtensorMap tm_uh;   // wavefield slots [slots][nx][ny][nzp] f32, halo box (TZ+2R4, TY+2R, 1, 1)
   CUtensorMap tm_uc;   // the same slots, centre box (TZ, TY, 1, 1)
-  CUtensorMap tm_m;    // model [nx][ny][nzp] (f32 / f16 / bf16), centre box (TZ, TY, 1)
+  CUtensorMap tm_m;    // model s = 1/m [nx][ny][nzp] (f32 / f16 / bf16), centre box (TZ, TY, 1)
   CUtensorMap tm_f;    // forward-wavefield slots (gradient), centre box (TZ, TY, 1, 1)
   CUtensorMap tm_e;    // damping field (eta*dt/2) [nx][ny][nzp] f32, centre box (optional)
   float* u;            // base of the wavefield slots
@@ -39,7 +39,7 @@ struct alignas(128) ShotDesc {
   const float* fwd;    // forward-wavefield slots (adjoint + gradient)
   long long fslot;
   float* acc;          // gradient accumulator, one slot (pitched)
-  const void* m;       // model, pitched, type mtype
+  const void* m;       // model as s = 1/m, pitched, type mtype
   const float* eta;    // eta*dt/2 profiles, [nx] then [ny] then [nz]
   const float* etaf;   // eta*dt/2 field, pitched (when kEtaField)
   int nx, ny, nz, nzp;

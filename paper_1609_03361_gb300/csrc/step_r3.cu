@@ -6,8 +6,8 @@ namespace fdw {
 
 const void* step_kernel_r3(int tile, bool grad) {
   switch (tile) {
-    case 0: return grad ? (const void*)&step_kernel<3, 2, 8, true> : (const void*)&step_kernel<3, 2, 8, false>;
-    case 1: return grad ? (const void*)&step_kernel<3, 4, 8, true> : (const void*)&step_kernel<3, 4, 8, false>;
+    case 0: return grad ? (const void*)&step_kernel<3, 1, 8, true> : (const void*)&step_kernel<3, 1, 8, false>;
+    case 1: return grad ? (const void*)&step_kernel<3, 2, 8, true> : (const void*)&step_kernel<3, 2, 8, false>;
     case 2: return grad ? (const void*)&step_kernel<3, 2, 4, true> : (const void*)&step_kernel<3, 2, 4, false>;
     case 3: return grad ? (const void*)&step_kernel<3, 1, 1, true> : (const void*)&step_kernel<3, 1, 1, false>;
     default: return nullptr;

@@ -6,8 +6,8 @@ namespace fdw {
 
 const void* step_kernel_r4(int tile, bool grad) {
   switch (tile) {
-    case 0: return grad ? (const void*)&step_kernel<4, 2, 8, true> : (const void*)&step_kernel<4, 2, 8, false>;
-    case 1: return grad ? (const void*)&step_kernel<4, 4, 8, true> : (const void*)&step_kernel<4, 4, 8, false>;
+    case 0: return grad ? (const void*)&step_kernel<4, 1, 8, true> : (const void*)&step_kernel<4, 1, 8, false>;
+    case 1: return grad ? (const void*)&step_kernel<4, 2, 8, true> : (const void*)&step_kernel<4, 2, 8, false>;
     case 2: return grad ? (const void*)&step_kernel<4, 2, 4, true> : (const void*)&step_kernel<4, 2, 4, false>;
     case 3: return grad ? (const void*)&step_kernel<4, 1, 1, true> : (const void*)&step_kernel<4, 1, 1, false>;
     default: return nullptr;
