@@ -227,7 +227,13 @@ def run_forward(args, world, rank, local):
     s.set_receivers(w.rec)
     q_dev = torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev)
     rec_dev = torch.empty((w.nt, w.rec.shape[0]), dtype=torch.float32, device=dev)
-    if not args.no_autotune:
+    if args.tiling:
+        t, lx, st = (int(v) for v in args.tiling.split(","))
+        s.set_tiling(t, lx, st)
+        s.set_model(m_dev)
+        s.set_sources(w.src)
+        s.set_receivers(w.rec)
+    elif not args.no_autotune:
         s.autotune(5)
     tiling = s.tiling()
     stream = torch.cuda.current_stream(dev)
@@ -327,6 +333,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tiling", default="", help="tile,xchunk,stages instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3

@@ -182,8 +182,9 @@ fdw_status fdw_sync(fdw_ctx* ctx);
  * cached there per (GPU, order, shape, model type).  Synchronises. */
 fdw_status fdw_autotune(fdw_ctx* ctx, int steps);
 
-/* Force a tile configuration: tile index (0..3, -1 = default), x-chunk length
- * (0 = default) and pipeline stages (0 = default). */
+/* Force a tile configuration: tile index (0..5, -1 = default; 3 is meant for
+ * 2D grids), x-chunk length (0 = default) and pipeline depth (>= 2, 0 =
+ * default). */
 fdw_status fdw_set_tiling(fdw_ctx* ctx, int tile, int xchunk, int stages);
 
 /* Tile configuration in use: out[0] = tile index, out[1] = x-chunk length,

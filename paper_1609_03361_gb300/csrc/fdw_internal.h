@@ -7,16 +7,17 @@
 
 namespace fdw {
 
-// Tile shapes of the step kernel: BY consumer warps; each half-warp covers NY
-// consecutive rows and each lane two z points, so a tile is (2 * BY * NY) x 32
-// points in (y, z).
+// Tile shapes of the step kernel: BY consumer warps; each quarter-warp covers
+// NY consecutive rows and each lane four z points, so a tile is (4 * BY * NY) x 32
+// points in (y, z).  Tiles 0 and 2 unroll the x loop so the register queue
+// rotates; the others shift it (smaller code).  Tile 3 is meant for 2D grids.
 struct TileShape {
   int ny_pts;
   int warps;
 };
-constexpr int kNumTiles = 4;
-constexpr TileShape kTiles[kNumTiles] = {{1, 8}, {2, 8}, {2, 4}, {1, 1}};
-constexpr int tile_rows(const TileShape& t) { return 2 * t.ny_pts * t.warps; }
+constexpr int kNumTiles = 6;
+constexpr TileShape kTiles[kNumTiles] = {{1, 4}, {2, 4}, {1, 8}, {1, 1}, {1, 4}, {2, 2}};
+constexpr int tile_rows(const TileShape& t) { return 4 * t.ny_pts * t.warps; }
 
 // Kernel registry: one translation unit per stencil radius.
 const void* step_kernel_r1(int tile, bool grad);

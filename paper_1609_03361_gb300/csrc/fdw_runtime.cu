@@ -470,6 +470,10 @@ static bool plan_etaf(const Plan& pl) {
 
 static void configure_kernel(const void* fn, size_t smem) {
   CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // all of the unified L1 / shared memory as shared memory: the pipeline
+  // stages are the working set, the kernel reads little through L1
+  CK(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                          (int)cudaSharedmemCarveoutMaxShared));
 }
 
 // Occupancy-limited number of resident CTAs of a launch.
@@ -1143,7 +1147,7 @@ static void plan_autotune(Plan& pl, int steps) {
       if (c->ny > 1) all2d = false;
       nxmax = std::max(nxmax, c->nx);
     }
-    std::vector<int> tiles = all2d ? std::vector<int>{3} : std::vector<int>{0, 1, 2};
+    std::vector<int> tiles = all2d ? std::vector<int>{3} : std::vector<int>{0, 1, 2, 4, 5};
     std::vector<int> lxs = {8, 16, 24, 32, 48, 64, 96, 128, nxmax};
     cudaStream_t s = pl.cap;
     cudaEvent_t e0, e1;
@@ -1152,7 +1156,7 @@ static void plan_autotune(Plan& pl, int steps) {
     float best = 1e30f;
     for (int t : tiles) {
       const int ms = max_stages(pl, t);
-      for (int extra : {2, 3, 5}) {
+      for (int extra : {2, 3, 4, 5}) {
         const int st = std::min(pl.r + 1 + extra, ms);
         for (int lx : lxs) {
           if (lx > nxmax && lx != nxmax) continue;

@@ -20,10 +20,10 @@
 //    which is the zero halo of the scheme), and for computed planes the
 //    u^{n-1}, m (and forward-wavefield / damping) tiles;
 //  - consumer warps keep the 2r+1 values of u^n along x of their points in
-//    registers (a queue whose slots rotate: the x loop is unrolled by 2r+1),
-//    take y and z neighbours from shared memory with 8-byte loads (each lane
-//    owns two z-neighbouring points, each half-warp NY rows), write u^{n+1}
-//    with 8-byte coalesced stores and release the stage;
+//    registers (a queue), take y and z neighbours from shared memory with
+//    16-byte loads (each lane owns four z-neighbouring points, each
+//    quarter-warp NY rows), write u^{n+1} with 16-byte coalesced stores and
+//    release the stage;
 //  - after the chunk, the consumers add the injected values into the nodes the
 //    unit owns (deterministic order, no atomics: no other CTA reads u^{n+1}
 //    during this step) and record the sampled points of u^n.
@@ -80,29 +80,38 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
 
 // Model values are stored as s = 1/m (squared velocity) in one of three types.
 template <typename MT>
-__device__ __forceinline__ float2 load_pair(const unsigned char* base, int i);
+__device__ __forceinline__ float4 load_quad(const unsigned char* base, int i);
 template <>
-__device__ __forceinline__ float2 load_pair<float>(const unsigned char* base, int i) {
-  return *reinterpret_cast<const float2*>(base + 4 * i);
+__device__ __forceinline__ float4 load_quad<float>(const unsigned char* base, int i) {
+  return *reinterpret_cast<const float4*>(base + 4 * i);
 }
 template <>
-__device__ __forceinline__ float2 load_pair<__half>(const unsigned char* base, int i) {
-  return __half22float2(*reinterpret_cast<const __half2*>(base + 2 * i));
+__device__ __forceinline__ float4 load_quad<__half>(const unsigned char* base, int i) {
+  const uint2 raw = *reinterpret_cast<const uint2*>(base + 2 * i);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+  return make_float4(a.x, a.y, b.x, b.y);
 }
 template <>
-__device__ __forceinline__ float2 load_pair<__nv_bfloat16>(const unsigned char* base, int i) {
-  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(base + 2 * i));
+__device__ __forceinline__ float4 load_quad<__nv_bfloat16>(const unsigned char* base, int i) {
+  const uint2 raw = *reinterpret_cast<const uint2*>(base + 2 * i);
+  const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
+  const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
+  return make_float4(a.x, a.y, b.x, b.y);
 }
 
-__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
-__device__ __forceinline__ float pick(const float2& a, int v) { return v ? a.y : a.x; }
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float pick(const float4& a, int v) {
+  return v == 0 ? a.x : (v == 1 ? a.y : (v == 2 ? a.z : a.w));
+}
 
-// Thread layout of a consumer warp: two half-warps, each on NY consecutive
-// rows (y) of the tile; every lane owns two neighbouring points along z.
-template <int NY>
+// Thread layout of a consumer warp: four quarter-warps of 8 lanes, each on NY
+// consecutive rows (y) of the tile; every lane owns four neighbouring points
+// along z, so a quarter-warp covers one 32-point row with 16-byte accesses.
+constexpr int kVZ = 4;
 struct Lanes {
   int r0;  // first local row of the thread
-  int zl;  // local z of the thread's first point (even)
+  int zl;  // local z of the thread's first point (multiple of 4)
 };
 
 #ifdef FDW_DEBUG_VERIFY
@@ -124,26 +133,29 @@ __device__ __forceinline__ void dbg_check(const char* what, float got, const flo
 #endif
 
 // Streams one work unit through the pipeline: warm-up of the x queue, then
-// one update per plane of [x0, x1).  Returns false if a wait gave up.
-template <int R, int NY, int BY, bool GRAD, typename MT>
+// one update per plane of [x0, x1).  XU: the x loop is unrolled by the queue
+// length 2R+1 so that the queue slots rotate; otherwise the queue shifts by one
+// slot per plane (smaller code).  Returns false if a wait gave up.
+template <int R, int NY, int BY, bool GRAD, bool XU, typename MT>
 __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, const ShotDesc* d,
                                          int u, const unsigned char* smem, uint32_t full0,
                                          uint32_t empty0, Cursor& ca, Cursor& cb,
-                                         volatile int* abort_flag, int lane, const Lanes<NY> L) {
+                                         volatile int* abort_flag, int lane, const Lanes L) {
   constexpr int TZ = kTZ;
   constexpr int R4 = Halo<R>::R4;
   constexpr int ZW = Halo<R>::ZW;
-  constexpr int Q = 2 * R + 1;  // x queue length; the x loop is unrolled by Q
+  constexpr int Q = 2 * R + 1;     // x queue length
+  constexpr int XS = XU ? Q : 1;   // planes per iteration of the x loop
+  constexpr int NW = 4 + 2 * R4;   // z window of a row: z-R4 .. z+3+R4
   const int S = P.stages;
-  const int nx = d->nx, ny = d->ny, nz = d->nz, nzp = d->nzp;
+  const int ny = d->ny, nz = d->nz, nzp = d->nzp;
   const bool etaf = (P.flags & kEtaField) != 0;
   const int r0 = L.r0, zl = L.zl;
   const int z = un.z0 + zl;
   const bool zin = z < nz;
-  (void)nx;
 
   // damping: y and z parts of the separable profile, per point
-  float eyz[NY][2];
+  float eyz[NY][kVZ];
   int rowoff[NY];
   bool rowok[NY];
 #pragma unroll
@@ -151,7 +163,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
     const int y = un.y0 + r0 + j;
     const float ey = (!etaf && y < ny) ? d->eta[d->nx + y] : 0.f;
 #pragma unroll
-    for (int v = 0; v < 2; ++v) {
+    for (int v = 0; v < kVZ; ++v) {
       const int zz = z + v;
       eyz[j][v] = ey + ((!etaf && zz < nz) ? d->eta[d->nx + ny + zz] : 0.f);
     }
@@ -160,8 +172,9 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
   }
   const long long plane = (long long)ny * nzp;
 
-  // x queue of centre values: slot (p - x0 + R) mod Q holds plane p
-  float qv[NY][2][Q];
+  // x queue of centre values: slot (p - x0 + R) mod Q holds plane p (XU), or
+  // slot i holds plane x - R + i (shift)
+  float qv[NY][kVZ][Q];
   bool ok = true;
 #pragma unroll
   for (int i = 0; i < 2 * R; ++i) {
@@ -169,9 +182,9 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
     const float* U = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes);
 #pragma unroll
     for (int j = 0; j < NY; ++j) {
-      const float2 cv = ok ? lds2(U + (r0 + j + R) * ZW + R4 + zl) : make_float2(0.f, 0.f);
-      qv[j][0][i] = cv.x;
-      qv[j][1][i] = cv.y;
+      const float4 cv = ok ? lds4(U + (r0 + j + R) * ZW + R4 + zl) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int v = 0; v < kVZ; ++v) qv[j][v][i] = pick(cv, v);
 #ifdef FDW_DEBUG_VERIFY
       dbg_check("warm", cv.x, d->u, (long long)P.cur * d->uslot, un.x0 - R + i, un.y0 + r0 + j,
                 z, d->nx, ny, nz, nzp, u);
@@ -186,11 +199,14 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
 
   float* uo = d->u + (long long)P.out * d->uslot;
   float* acc = d->acc;
+  const float* eta_x = d->eta;
+  float ex_next = etaf ? 0.f : eta_x[un.x0];  // x part of the damping, one plane ahead
 #pragma unroll 1
-  for (int xb = un.x0; xb < un.x1; xb += Q) {
+  for (int xb = un.x0; xb < un.x1; xb += XS) {
 #pragma unroll
-    for (int t = 0; t < Q; ++t) {
-      const int x = xb + t;
+    for (int t0 = 0; t0 < XS; ++t0) {
+      const int t = XU ? t0 : 0;
+      const int x = xb + t0;
       if (x >= un.x1) break;
       // centre values of plane x+R join the queue
       if (!wait_or_abort(full0 + 8 * ca.stage, ca.phase, abort_flag)) return false;
@@ -198,96 +214,122 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
         const float* Ua = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes);
 #pragma unroll
         for (int j = 0; j < NY; ++j) {
-          const float2 cv = lds2(Ua + (r0 + j + R) * ZW + R4 + zl);
-          qv[j][0][(t + 2 * R) % Q] = cv.x;
-          qv[j][1][(t + 2 * R) % Q] = cv.y;
+          const float4 cv = lds4(Ua + (r0 + j + R) * ZW + R4 + zl);
+#pragma unroll
+          for (int v = 0; v < kVZ; ++v) qv[j][v][(t + 2 * R) % Q] = pick(cv, v);
 #ifdef FDW_DEBUG_VERIFY
           dbg_check("ahead", cv.x, d->u, (long long)P.cur * d->uslot, x + R, un.y0 + r0 + j, z,
                     d->nx, ny, nz, nzp, u);
 #endif
         }
       }
+      // a look-ahead plane past the chunk is only needed for its centre
+      // values; it is handed back after the update below has consumed them
       const int ahead_stage = ca.stage;
       ca.next(S);
 
       // neighbours in y and z of plane x from the staged halo plane
       const unsigned char* sb = smem + cb.stage * P.stage_bytes;
       const float* U = reinterpret_cast<const float*>(sb);
-      float2 yr[NY + 2 * R];
-      float wz[NY][2 + 2 * R4];
-#pragma unroll
-      for (int i = 0; i < R; ++i) {
-        yr[i] = lds2(U + (r0 + i) * ZW + R4 + zl);
-        yr[NY + R + i] = lds2(U + (r0 + NY + R + i) * ZW + R4 + zl);
-      }
-#pragma unroll
-      for (int j = 0; j < NY; ++j) {
-#pragma unroll
-        for (int i = 0; i <= R4; ++i) {
-          const float2 w2 = lds2(U + (r0 + j + R) * ZW + zl + 2 * i);
-          wz[j][2 * i] = w2.x;
-          wz[j][2 * i + 1] = w2.y;
-        }
-        yr[R + j] = make_float2(wz[j][R4], wz[j][R4 + 1]);
-      }
-      const float ex = etaf ? 0.f : d->eta[x];
+      const float ex = ex_next;
+      if (!etaf && x + 1 < un.x1) ex_next = eta_x[x + 1];
       const float* Pp = reinterpret_cast<const float*>(sb + P.off_p);
       const long long xoff = (long long)x * plane;
+      // y neighbours of the thread's rows: local rows r0-R .. r0+NY-1+R
+      float4 yr[NY + 2 * R];
+      float val[NY][kVZ];
+      float d2t[NY][kVZ];
+      float4 fw[NY];
+      (void)d2t;
+      (void)fw;
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        yr[i] = lds4(U + (r0 + i) * ZW + R4 + zl);
+        yr[NY + R + i] = lds4(U + (r0 + NY + R + i) * ZW + R4 + zl);
+      }
+      // with several rows per thread, each row's centre is a y neighbour of
+      // the others: load all of them before any row is updated
+      if (NY > 1) {
+#pragma unroll
+        for (int j = 0; j < NY; ++j) yr[R + j] = lds4(U + (r0 + j + R) * ZW + R4 + zl);
+      }
 #pragma unroll
       for (int j = 0; j < NY; ++j) {
-        const int li = (r0 + j) * TZ + zl;
-        const float2 pv = lds2(Pp + li);
-        const float2 sv = load_pair<MT>(sb + P.off_m, li);
-        float2 ev;
-        if (etaf) ev = lds2(reinterpret_cast<const float*>(sb + P.off_e) + li);
-        else ev = make_float2(ex + eyz[j][0], ex + eyz[j][1]);
-        float val[2], cc[2];
+        float wz[NW];
 #pragma unroll
-        for (int v = 0; v < 2; ++v) {
-          const float c = wz[j][R4 + v];
+        for (int i = 0; i < NW / 4; ++i) {
+          const float4 w4 = lds4(U + (r0 + j + R) * ZW + zl + 4 * i);
+          wz[4 * i] = w4.x;
+          wz[4 * i + 1] = w4.y;
+          wz[4 * i + 2] = w4.z;
+          wz[4 * i + 3] = w4.w;
+        }
+        const int li = (r0 + j) * TZ + zl;
+        const float4 pv = lds4(Pp + li);
+        const float4 sv = load_quad<MT>(sb + P.off_m, li);
+        float4 ev;
+        if (etaf) ev = lds4(reinterpret_cast<const float*>(sb + P.off_e) + li);
+        else ev = make_float4(ex + eyz[j][0], ex + eyz[j][1], ex + eyz[j][2], ex + eyz[j][3]);
+#pragma unroll
+        for (int v = 0; v < kVZ; ++v) {
+          const float c = wz[R4 + v];
           float lx = 0.f, ly = 0.f, lz = 0.f;
 #pragma unroll
           for (int k = 1; k <= R; ++k) {
             lx = fmaf(P.w[0][k], qv[j][v][(t + R - k) % Q] + qv[j][v][(t + R + k) % Q], lx);
             ly = fmaf(P.w[1][k], pick(yr[R + j - k], v) + pick(yr[R + j + k], v), ly);
-            lz = fmaf(P.w[2][k], wz[j][R4 + v - k] + wz[j][R4 + v + k], lz);
+            lz = fmaf(P.w[2][k], wz[R4 + v - k] + wz[R4 + v + k], lz);
           }
           const float lap = fmaf(P.csum, c, lx + ly + lz);
-          const float s = pick(sv, v), e = pick(ev, v), prev = pick(pv, v);
-          const float es = e * s;
+          const float sm = pick(sv, v), e = pick(ev, v), prev = pick(pv, v);
+          const float es = e * sm;
           // [2u - (1 - e s) u- + s dt^2 L u] / (1 + e s): the three-level update divided by m
-          const float num = fmaf(es, prev, fmaf(s, lap, 2.f * c) - prev);
-          val[v] = __fdividef(num, 1.f + es);
-          cc[v] = c;
+          const float num = fmaf(es, prev, fmaf(sm, lap, 2.f * c) - prev);
+          val[j][v] = __fdividef(num, 1.f + es);
+          if (GRAD) d2t[j][v] = val[j][v] - 2.f * c + prev;  // second time difference of lambda
         }
+        if (GRAD) fw[j] = lds4(reinterpret_cast<const float*>(sb + P.off_f) + li);
+      }
+      // every read of the staged planes is done: hand them back before the
+      // global stores, which only read registers
+      release_stage(empty0 + 8 * cb.stage, lane);
+      if (x + R >= un.x1) release_stage(empty0 + 8 * ahead_stage, lane);
+      cb.next(S);
+#pragma unroll
+      for (int j = 0; j < NY; ++j) {
         if (rowok[j]) {
           const long long off = xoff + rowoff[j];
-          *reinterpret_cast<float2*>(uo + off) = make_float2(val[0], val[1]);
+          *reinterpret_cast<float4*>(uo + off) =
+              make_float4(val[j][0], val[j][1], val[j][2], val[j][3]);
           if (GRAD) {
-            const float2 f = lds2(reinterpret_cast<const float*>(sb + P.off_f) + li);
-            float2 a = *reinterpret_cast<const float2*>(acc + off);
-            a.x = fmaf(f.x, val[0] - 2.f * cc[0] + pv.x, a.x);
-            a.y = fmaf(f.y, val[1] - 2.f * cc[1] + pv.y, a.y);
-            *reinterpret_cast<float2*>(acc + off) = a;
+            float4 a = *reinterpret_cast<const float4*>(acc + off);
+            a.x = fmaf(fw[j].x, d2t[j][0], a.x);
+            a.y = fmaf(fw[j].y, d2t[j][1], a.y);
+            a.z = fmaf(fw[j].z, d2t[j][2], a.z);
+            a.w = fmaf(fw[j].w, d2t[j][3], a.w);
+            *reinterpret_cast<float4*>(acc + off) = a;
           }
         }
       }
-      release_stage(empty0 + 8 * cb.stage, lane);
-      // a look-ahead plane past the chunk is only needed for its centre
-      // value; it is handed back after the update has consumed it
-      if (x + R >= un.x1) release_stage(empty0 + 8 * ahead_stage, lane);
-      cb.next(S);
+      if (!XU) {
+#pragma unroll
+        for (int j = 0; j < NY; ++j)
+#pragma unroll
+          for (int v = 0; v < kVZ; ++v)
+#pragma unroll
+            for (int i = 0; i < 2 * R; ++i) qv[j][v][i] = qv[j][v][i + 1];
+      }
     }
   }
   cb.skip(R, S);
   return true;
 }
 
-template <int R, int NY, int BY, bool GRAD>
+template <int R, int NY, int BY, bool GRAD, bool XU>
 __global__ void __launch_bounds__((BY + 1) * 32)
 step_kernel(const __grid_constant__ StepParams P) {
   constexpr int TZ = kTZ;
-  constexpr int TY = 2 * BY * NY;
+  constexpr int TY = 4 * BY * NY;
   constexpr int R4 = Halo<R>::R4;
   constexpr int ZW = Halo<R>::ZW;
   constexpr int YW = TY + 2 * R;
@@ -356,9 +398,9 @@ step_kernel(const __grid_constant__ StepParams P) {
     }
   } else {
     // ------------------------------ consumers -----------------------------
-    Lanes<NY> L;
-    L.r0 = warp * 2 * NY + (lane >> 4) * NY;
-    L.zl = 2 * (lane & 15);
+    Lanes L;
+    L.r0 = warp * 4 * NY + (lane >> 3) * NY;
+    L.zl = kVZ * (lane & 7);
     Cursor ca{0, 0u};   // read-ahead cursor: every plane in order (centre values)
     Cursor cb{0, 0u};   // compute cursor: the plane being updated
     uint32_t tail_phase = 0u;
@@ -369,13 +411,13 @@ step_kernel(const __grid_constant__ StepParams P) {
       const ShotDesc* d = P.shots + un.shot;
       const int mtype = d->mtype;
       if (mtype == kF16)
-        ok = run_unit<R, NY, BY, GRAD, __half>(P, un, d, u, smem, full0, empty0, ca, cb,
+        ok = run_unit<R, NY, BY, GRAD, XU, __half>(P, un, d, u, smem, full0, empty0, ca, cb,
                                                abort_flag, lane, L);
       else if (mtype == kBF16)
-        ok = run_unit<R, NY, BY, GRAD, __nv_bfloat16>(P, un, d, u, smem, full0, empty0, ca, cb,
+        ok = run_unit<R, NY, BY, GRAD, XU, __nv_bfloat16>(P, un, d, u, smem, full0, empty0, ca, cb,
                                                       abort_flag, lane, L);
       else
-        ok = run_unit<R, NY, BY, GRAD, float>(P, un, d, u, smem, full0, empty0, ca, cb,
+        ok = run_unit<R, NY, BY, GRAD, XU, float>(P, un, d, u, smem, full0, empty0, ca, cb,
                                               abort_flag, lane, L);
       if (!ok) break;
 

@@ -6,10 +6,18 @@ namespace fdw {
 
 const void* step_kernel_r7(int tile, bool grad) {
   switch (tile) {
-    case 0: return grad ? (const void*)&step_kernel<7, 1, 8, true> : (const void*)&step_kernel<7, 1, 8, false>;
-    case 1: return grad ? (const void*)&step_kernel<7, 2, 8, true> : (const void*)&step_kernel<7, 2, 8, false>;
-    case 2: return grad ? (const void*)&step_kernel<7, 2, 4, true> : (const void*)&step_kernel<7, 2, 4, false>;
-    case 3: return grad ? (const void*)&step_kernel<7, 1, 1, true> : (const void*)&step_kernel<7, 1, 1, false>;
+    case 0: return grad ? (const void*)&step_kernel<7, 1, 4, true, true>
+                          : (const void*)&step_kernel<7, 1, 4, false, true>;
+    case 1: return grad ? (const void*)&step_kernel<7, 2, 4, true, false>
+                          : (const void*)&step_kernel<7, 2, 4, false, false>;
+    case 2: return grad ? (const void*)&step_kernel<7, 1, 8, true, true>
+                          : (const void*)&step_kernel<7, 1, 8, false, true>;
+    case 3: return grad ? (const void*)&step_kernel<7, 1, 1, true, false>
+                          : (const void*)&step_kernel<7, 1, 1, false, false>;
+    case 4: return grad ? (const void*)&step_kernel<7, 1, 4, true, false>
+                          : (const void*)&step_kernel<7, 1, 4, false, false>;
+    case 5: return grad ? (const void*)&step_kernel<7, 2, 2, true, false>
+                          : (const void*)&step_kernel<7, 2, 2, false, false>;
     default: return nullptr;
   }
 }
