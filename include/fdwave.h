@@ -216,6 +216,34 @@ fdw_status fdw_batch_gradient(fdw_batch* b, const float* const* resid,
 fdw_status fdw_batch_autotune(fdw_batch* b, int steps);
 fdw_status fdw_batch_get_tiling(fdw_batch* b, int* out5);
 
+/* ---------------------------------------------------------- allocation-free */
+
+/* Forward modelling that allocates nothing.  The paper has no counterpart:
+ * this is a service for callers that cannot call cudaMalloc, such as code
+ * that must stay inside a device-memory budget owned by another allocator or
+ * a loop that may not touch the allocator once it runs.  It computes what
+ * fdw_create + fdw_set_model (physical layout, FDW_F32) + fdw_set_sources +
+ * fdw_set_receivers + fdw_forward compute, with the built-in damping, for a
+ * small problem, keeping all of its scratch (wavefields, model, tables) in one
+ * 16 MiB static device array that every GPU loading the library holds until
+ * the process exits.
+ *   m     device, float32, physical shape (squared slowness, > 0)
+ *   q     device, float32 [nt][nsrc];  rec  device, float32 [nt][nrec] (out)
+ *   src_xyz, rec_xyz  host, double [n][ndim], metres
+ *   other arguments as in fdw_create.
+ * Limits: at most 4096 computational points per axis, at most 2^20 points per
+ * field with rows padded to a multiple of 32, at most 4096 sources and 4096
+ * receivers, at most 8192 work units; FDW_ERR_SHAPE beyond them.  The first
+ * call on a device looks up the array's device address, so make it before any
+ * stream capture.  Every call rewrites the array and clears the wavefields;
+ * calls that overlap on the GPU (other streams or host threads) race on it.
+ * The call waits for its stream and returns FDW_ERR_TIMEOUT if a device-side
+ * bounded wait gave up. */
+fdw_status fdw_forward_static(int ndim, const int64_t* shape, const double* spacing,
+                              int space_order, int nbl, double dt, int nt, double vmax,
+                              const float* m, int nsrc, const double* src_xyz, const float* q,
+                              int nrec, const double* rec_xyz, float* rec, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,8 @@ _SIGS = [
     ("fdw_batch_gradient", _I, [_P, _PP, _PP, _PP, _I, _P]),
     ("fdw_batch_autotune", _I, [_P, _I]),
     ("fdw_batch_get_tiling", _I, [_P, ctypes.POINTER(_I)]),
+    ("fdw_forward_static", _I, [_I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), _I, _I,
+                                _D, _I, _D, _P, _I, _P, _P, _I, _P, _P, _P]),
 ]
 
 
@@ -308,6 +310,23 @@ def fdw_batch_get_tiling(b):
     out = (ctypes.c_int * 5)()
     _check(lib().fdw_batch_get_tiling(b, out), batch=b)
     return dict(zip(("tile", "xchunk", "stages", "ctas", "units"), list(out)))
+
+
+def fdw_forward_static(shape, spacing, space_order, nbl, dt, nt, vmax, m, src_xyz, q, rec_xyz,
+                       rec, stream=None, device=0):
+    """Allocation-free forward modelling of a small problem (see include/fdwave.h):
+    m, q and rec must be device arrays (torch CUDA tensors); coordinates are host."""
+    keep = []
+    ndim = len(shape)
+    sh = (ctypes.c_int64 * ndim)(*[int(v) for v in shape])
+    sp = np.broadcast_to(np.asarray(spacing, dtype=np.float64), (ndim,)).copy()
+    src = np.ascontiguousarray(src_xyz, dtype=np.float64).reshape(-1, ndim)
+    rcv = np.ascontiguousarray(rec_xyz, dtype=np.float64).reshape(-1, ndim)
+    _check(lib().fdw_forward_static(ndim, sh, sp.ctypes.data_as(ctypes.POINTER(_D)),
+                                    int(space_order), int(nbl), float(dt), int(nt), float(vmax),
+                                    _ptr(m, keep), src.shape[0], _ptr(src, keep, np.float64),
+                                    _ptr(q, keep), rcv.shape[0], _ptr(rcv, keep, np.float64),
+                                    _ptr(rec, keep), _stream(stream, device)))
 
 
 # ------------------------------------------------------------------ objects
