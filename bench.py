@@ -305,6 +305,11 @@ def run_forward(args, world, rank, local):
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
         base = cpu_baseline(w)
 
+    extras = {}
+    if not args.no_extras:
+        extras["batched"] = run_batched(args.batch_shots, 800, dev)
+        extras["fwi"] = run_fwi(args.fwi_shots, args.fwi_nt, 10, dev)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GPts/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -318,8 +323,133 @@ def run_forward(args, world, rank, local):
                            "tiling": tiling},
                 "roofline": roofline, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk}
+        line.update(extras)
         print(json.dumps(line), flush=True)
     s.close()
+
+
+def run_batched(nshots, nt, dev, timed_reps=1):
+    """Batched forward: nshots uneven cubes (96^3..192^3 physical, +40-point
+    layer), SO8, nt steps, one launch per time step over all shots, against
+    the same shots run one after the other.  Returns a dict."""
+    import torch
+    from paper_1609_03361_gb300 import fdwave as fw
+    from paper_1609_03361_gb300 import workloads as W
+    shots = W.batched_shots(nshots=nshots, nt=nt)
+    vmax = max(w.vmax for w in shots)
+    dt = W.choose_dt(fw.fdw_dt_max(3, shots[0].spacing, 8, vmax))
+    solvers, qs, recs = [], [], []
+    for w in shots:
+        w.dt = dt
+        s = fw.Solver(w.shape, w.spacing, 8, w.nbl, dt, nt, vmax, device=dev.index or 0)
+        s.set_model(torch.from_numpy(w.m.astype(np.float32)).to(dev))
+        s.set_sources(w.src)
+        s.set_receivers(w.rec)
+        solvers.append(s)
+        qs.append(torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev))
+        recs.append(torch.empty((nt, w.rec.shape[0]), device=dev))
+    updates = sum(int(np.prod(w.comp_shape)) for w in shots) * (nt - 1)
+    b = fw.Batch(solvers)
+    b.autotune(3)
+    b.forward(qs, recs)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(timed_reps):
+        b.forward(qs, recs)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_batch = e0.elapsed_time(e1) / 1e3 / timed_reps
+    ref = [r.clone() for r in recs]
+    b.close()
+    for s, q, r in zip(solvers, qs, recs):   # warm each plain path once
+        s.forward(q, r)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for _ in range(timed_reps):
+        for s, q, r in zip(solvers, qs, recs):
+            s.forward(q, r)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    t_plain = e0.elapsed_time(e1) / 1e3 / timed_reps
+    same = all(bool(torch.equal(a, c)) for a, c in zip(ref, recs))
+    for s in solvers:
+        s.close()
+    return {"workload": f"{nshots} shots, cubes of {min(w.shape[0] for w in shots)}^3.."
+                        f"{max(w.shape[0] for w in shots)}^3 (+40-point layer), SO8, {nt} steps",
+            "gpts_batched": updates / t_batch / 1e9, "gpts_plain": updates / t_plain / 1e9,
+            "s_batched": t_batch, "s_plain": t_plain, "traces_identical": same}
+
+
+def run_fwi(nshots, nt, k, dev):
+    """FWI gradient of J = 1/2 sum |P_r u - d_obs|^2 over nshots shots on the
+    256^3 SO8 model (observed data from the model with a +5% Gaussian anomaly):
+    plain = shots one by one with FP32 checkpoints; batched = all shots per
+    launch with FP16 snapshots (one float32 scale each).  Returns s/shot for
+    both and the relative L2 difference of the summed gradients."""
+    import torch
+    from paper_1609_03361_gb300 import fdwave as fw
+    from paper_1609_03361_gb300 import workloads as W
+    shots, v_true = W.fwi_shots(nt=nt, nshots=nshots)
+    base = shots[0]
+    vmax = float(max(base.velocity.max(), v_true.max()))
+    dt = W.choose_dt(fw.fdw_dt_max(3, base.spacing, base.space_order, vmax))
+    m0 = torch.from_numpy(base.m.astype(np.float32)).to(dev)
+    mt = torch.from_numpy((1.0 / v_true ** 2).astype(np.float32)).to(dev)
+    for w in shots:
+        w.dt = dt
+    qs = [torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev) for w in shots]
+    nrec = base.rec.shape[0]
+    # observed data and the plain per-shot gradient with one reused solver
+    s = fw.Solver(base.shape, base.spacing, base.space_order, base.nbl, dt, nt, vmax,
+                  device=dev.index or 0)
+    s.set_receivers(base.rec)
+    dobs = []
+    s.set_model(mt)
+    for w, q in zip(shots, qs):
+        s.set_sources(w.src)
+        dobs.append(s.forward(q))
+    s.set_model(m0)
+    rec = torch.empty((nt, nrec), device=dev)
+    g_plain = torch.zeros(base.comp_shape, device=dev, dtype=torch.float64)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for w, q, d in zip(shots, qs, dobs):
+        s.set_sources(w.src)
+        s.forward_ckpt(q, k, "f32", rec=rec)
+        g_plain += s.gradient(rec, d).double()
+    torch.cuda.synchronize(dev)
+    t_plain = time.perf_counter() - t0
+    s.close()
+    # batched with FP16 snapshots
+    solvers = []
+    for w in shots:
+        sv = fw.Solver(base.shape, base.spacing, base.space_order, base.nbl, dt, nt, vmax,
+                       device=dev.index or 0)
+        sv.set_model(m0)
+        sv.set_sources(w.src)
+        sv.set_receivers(base.rec)
+        solvers.append(sv)
+    b = fw.Batch(solvers)
+    recs = [torch.empty((nt, nrec), device=dev) for _ in shots]
+    b.forward_ckpt(qs, k, "f16", recs=recs)   # allocation and graph capture, untimed
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    b.forward_ckpt(qs, k, "f16", recs=recs)
+    grads = b.gradient(recs, dobs)
+    g_batch = torch.zeros_like(g_plain)
+    for g in grads:
+        g_batch += g.double()
+    torch.cuda.synchronize(dev)
+    t_batch = time.perf_counter() - t0
+    diff = float(torch.linalg.vector_norm(g_batch - g_plain) / torch.linalg.vector_norm(g_plain))
+    b.close()
+    for sv in solvers:
+        sv.close()
+    return {"workload": f"{nshots} shots, 256^3 (336^3 computational), SO8, {nt} steps, "
+                        f"checkpoints every {k} steps",
+            "s_per_shot_plain_fp32": t_plain / nshots, "s_per_shot_batched_fp16": t_batch / nshots,
+            "grad_rel_l2_batched_fp16_vs_plain_fp32": diff}
 
 
 def main():
@@ -334,6 +464,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tiling", default="", help="tile,xchunk,stages instead of autotuning")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and FWI parts")
+    ap.add_argument("--batch-shots", type=int, default=64)
+    ap.add_argument("--fwi-shots", type=int, default=4)
+    ap.add_argument("--fwi-nt", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3

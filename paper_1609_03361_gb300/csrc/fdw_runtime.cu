@@ -1148,7 +1148,7 @@ static void plan_autotune(Plan& pl, int steps) {
       nxmax = std::max(nxmax, c->nx);
     }
     std::vector<int> tiles = all2d ? std::vector<int>{3} : std::vector<int>{0, 1, 2, 4, 5};
-    std::vector<int> lxs = {8, 16, 24, 32, 48, 64, 96, 128, nxmax};
+    std::vector<int> lxs = {16, 32, 64, 128, nxmax};
     cudaStream_t s = pl.cap;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -1156,7 +1156,7 @@ static void plan_autotune(Plan& pl, int steps) {
     float best = 1e30f;
     for (int t : tiles) {
       const int ms = max_stages(pl, t);
-      for (int extra : {2, 3, 4, 5}) {
+      for (int extra : {2, 3}) {
         const int st = std::min(pl.r + 1 + extra, ms);
         for (int lx : lxs) {
           if (lx > nxmax && lx != nxmax) continue;
