@@ -1,0 +1,104 @@
+"""FWI gradient through the CUDA path: Taylor test, central finite differences
+of the GPU misfit, and the torch.autograd.Function wrapper.
+
+Tolerances: the Taylor remainder must fall by ~4x per halving (second order)
+over the range where FP32 rounding of the misfit stays below it; the
+finite-difference check holds to 1e-3 relative (FP32 traces)."""
+import numpy as np
+import pytest
+
+from problems import Problem, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_03361_gb300 import build, fdwave
+    build.build()
+    fdwave.lib()
+    return fdwave
+
+
+def _setup(fw):
+    pb = Problem((26, 24, 28), 10.0, 8, 6, 150, nsrc=1, nrec=12, seed=91, vfac=0.8)
+    rng = np.random.default_rng(4)
+    v_true = pb.v * (1 + 0.03 * rng.standard_normal(pb.shape))
+    s = pb.solver(fw)
+    s.set_model((1 / v_true ** 2).astype(np.float32))
+    d = s.forward(pb.q32).astype(np.float64)
+    s.set_model(pb.m32)
+    return pb, s, d
+
+
+def _J(s, m, q, d):
+    s.set_model(m.astype(np.float32))
+    r = s.forward(q).astype(np.float64) - d
+    return 0.5 * float(np.sum(r * r)), r
+
+
+def test_taylor_second_order(fw):
+    pb, s, d = _setup(fw)
+    m0 = pb.m32.astype(np.float64)
+    J0, r = _J(s, m0, pb.q32, d)
+    s.set_model(pb.m32)
+    s.forward_ckpt(pb.q32, 10, "f32")
+    g = s.gradient(r.astype(np.float32), None, "physical").astype(np.float64)
+    dm = np.random.default_rng(2).standard_normal(pb.shape) * m0.mean()
+    gd = float(np.sum(g * dm))
+    errs = []
+    for k in range(4):
+        h = 2e-2 / 2 ** k
+        Jh, _ = _J(s, m0 + h * dm, pb.q32, d)
+        errs.append(abs(Jh - J0 - h * gd))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    s.close()
+    assert all(3.0 < x < 5.0 for x in ratios), (ratios, errs)
+
+
+def test_gradient_matches_central_differences(fw):
+    pb, s, d = _setup(fw)
+    m0 = pb.m32.astype(np.float64)
+    J0, r = _J(s, m0, pb.q32, d)
+    s.set_model(pb.m32)
+    s.forward_ckpt(pb.q32, 7, "f32")
+    g = s.gradient(r.astype(np.float32), None, "physical").astype(np.float64)
+    rng = np.random.default_rng(6)
+    for _ in range(3):
+        dm = rng.standard_normal(pb.shape) * m0.mean()
+        eps = 2e-3
+        Jp, _ = _J(s, m0 + eps * dm, pb.q32, d)
+        Jm, _ = _J(s, m0 - eps * dm, pb.q32, d)
+        fd = (Jp - Jm) / (2 * eps)
+        an = float(np.sum(g * dm))
+        assert abs(fd - an) <= 1e-3 * abs(fd), (fd, an)
+    s.close()
+
+
+def test_autograd_function_matches_oracle(fw):
+    pb = Problem((22, 20, 24), 10.0, 4, 5, 90, nsrc=1, nrec=8, seed=93)
+    dev = torch.device("cuda", 0)
+    s = pb.solver(fw)
+    d = torch.from_numpy(np.random.default_rng(8).standard_normal((pb.nt, 8)).astype(np.float32)).to(dev)
+    m = torch.from_numpy(pb.m32).to(dev).requires_grad_(True)
+    q = torch.from_numpy(pb.q32).to(dev)
+    rec = fw.fwi_traces(m, s, q, 6, "f32")
+    loss = 0.5 * ((rec - d) ** 2).sum()
+    loss.backward()
+    g = m.grad.detach().cpu().numpy()
+    # oracle: gradient w.r.t. the computational model, folded onto the physical edges
+    ref = pb.oracle_gradient((rec.detach() - d).cpu().numpy().astype(np.float64))
+    nbl = pb.nbl
+    fold = np.zeros(pb.shape)
+    n = ref.shape
+    for x in range(n[0]):
+        for y in range(n[1]):
+            cx = min(max(x - nbl, 0), pb.shape[0] - 1)
+            cy = min(max(y - nbl, 0), pb.shape[1] - 1)
+            cz = np.clip(np.arange(n[2]) - nbl, 0, pb.shape[2] - 1)
+            np.add.at(fold[cx, cy], cz, ref[x, y])
+    s.close()
+    assert rel_l2(g, fold) < 1e-4

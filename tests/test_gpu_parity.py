@@ -259,3 +259,53 @@ def test_autotune_keeps_results(fw):
     s.sync()
     s.close()
     assert rel_l2(rec, pb.oracle_forward()) < TOL
+
+
+def test_config_2d_101_so4_500_steps(fw):
+    """The 2D workload exactly: 101^2 at 10 m, SO4, 40-point layer, 1.5 km/s,
+    10 Hz Ricker at the centre, 101 on-grid receivers at 20 m depth, 500 steps."""
+    import oracle
+    from paper_1609_03361_gb300 import workloads as W
+    w = W.config_2d_small()
+    w.dt = W.choose_dt(oracle.dt_max(2, w.spacing, w.space_order, w.vmax))
+    s = fw.Solver(w.shape, w.spacing, w.space_order, w.nbl, w.dt, w.nt, w.vmax)
+    s.set_model(w.m.astype(np.float32))
+    s.set_sources(w.src)
+    s.set_receivers(w.rec)
+    q = w.wavelet().astype(np.float32)[:, None]
+    rec = s.forward(q)
+    s.sync()
+    s.close()
+    st = oracle.Setup(w.shape, w.spacing, w.space_order, w.nbl, w.dt, w.nt)
+    M = oracle.extend_model(st, w.m.astype(np.float32).astype(np.float64))
+    ref = oracle.forward(st, M, oracle.damping(st, w.vmax), w.src, q.astype(np.float64), w.rec)
+    assert rel_l2(rec, ref) < TOL
+
+
+def test_config_3d_256_so8_full_grid_first_steps(fw):
+    """The 256^3 SO8 workload on its full 336^3 computational grid and in the
+    tiling the benchmark uses, compared with the oracle over its first 24
+    steps (the oracle needs ~1 s per step on this grid)."""
+    import oracle
+    from paper_1609_03361_gb300 import workloads as W
+    nt = 24
+    w = W.config_3d(256, 12.5, 8, nt)
+    w.dt = W.choose_dt(oracle.dt_max(3, w.spacing, w.space_order, w.vmax))
+    dev = torch.device("cuda", 0)
+    s = fw.Solver(w.shape, w.spacing, w.space_order, w.nbl, w.dt, w.nt, w.vmax)
+    s.set_model(torch.from_numpy(w.m.astype(np.float32)).to(dev))
+    s.set_sources(w.src)
+    s.set_receivers(w.rec)
+    q = torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev)
+    s.autotune(2)
+    rec = s.forward(q).cpu().numpy()
+    u = s.wavefield(0, like=q).cpu().numpy()
+    s.sync()
+    s.close()
+    st = oracle.Setup(w.shape, w.spacing, w.space_order, w.nbl, w.dt, nt)
+    M = oracle.extend_model(st, w.m.astype(np.float32).astype(np.float64))
+    ref, uref = oracle.forward(st, M, oracle.damping(st, w.vmax), w.src,
+                               q.cpu().numpy().astype(np.float64), w.rec, final=True)
+    assert np.abs(ref).max() > 0
+    assert rel_l2(rec, ref) < TOL
+    assert rel_l2(u, uref) < TOL
