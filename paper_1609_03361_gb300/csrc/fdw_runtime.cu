@@ -301,6 +301,7 @@ struct Plan {
   std::vector<double> weights;       // unscaled second-derivative weights c_0..c_r
   bool built = false;
   int max_rec = 0, max_src = 0;
+  bool test_stall = false;  // FDW_TEST_STALL: make every step's waits run out (tests only)
   long long max_points = 0;
 
   void clear_graphs() {
@@ -757,7 +758,7 @@ static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s) {
   P.shots = pl.d_desc[a.role];
   P.units = pl.d_units;
   P.nunits = nunits;
-  P.flags = a.flags | (etaf ? kEtaField : 0);
+  P.flags = a.flags | (etaf ? kEtaField : 0) | (pl.test_stall ? kTestStall : 0);
   P.inj_ptr = Ls.d_inj_ptr;
   P.inj_nodes = Ls.d_nodes;
   P.inj_terms = Ls.d_terms;
@@ -1009,6 +1010,7 @@ static void check_compatible(const std::vector<fdw_ctx*>& v) {
 static void plan_forward(Plan& pl, const float* const* q, float* const* rec, int k, int stype,
                          cudaStream_t s) {
   const size_t ns = pl.shots.size();
+  pl.test_stall = env_flag("FDW_TEST_STALL") && env_flag("FDW_NO_GRAPH");
   std::vector<std::pair<float*, float*>> copies;  // (host dst, staging src)
   std::vector<size_t> sizes;
   for (size_t i = 0; i < ns; ++i) {

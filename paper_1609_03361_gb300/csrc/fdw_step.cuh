@@ -367,7 +367,8 @@ step_kernel(const __grid_constant__ StepParams P) {
       Cursor c{0, 0u};
       int issued = 0;
       const uint32_t bytes_u = YW * ZW * 4;
-      for (int u = blockIdx.x; u < P.nunits && !*abort_flag; u += gridDim.x) {
+      for (int u = blockIdx.x; u < P.nunits && !*abort_flag && !(P.flags & kTestStall);
+           u += gridDim.x) {
         const Unit un = P.units[u];
         const ShotDesc* d = P.shots + un.shot;
         const uint32_t bytes_in = TY * TZ * 4 + TY * TZ * (d->mtype == kF32 ? 4 : 2) +

@@ -25,6 +25,8 @@ enum StepFlags : int {
   kSample = 2,       // record the sampling list of each unit from the current field
   kEtaField = 4,     // damping read from a full field instead of 1-D profiles
   kInjectDiff = 8,   // inject (a - b) instead of a
+  kTestStall = 16,   // test hook: the producer issues no loads, so every consumer
+                     // wait runs out of its clock budget and reports an error
 };
 
 // Per-shot description; lives in device memory, 128-byte aligned (tensor maps).
