@@ -381,7 +381,7 @@ def run_batched(nshots, nt, dev, timed_reps=1):
             "s_batched": t_batch, "s_plain": t_plain, "traces_identical": same}
 
 
-def run_fwi(nshots, nt, k, dev):
+def run_fwi(nshots, nt, k, dev, group=4):
     """FWI gradient of J = 1/2 sum |P_r u - d_obs|^2 over nshots shots on the
     256^3 SO8 model (observed data from the model with a +5% Gaussian anomaly):
     plain = shots one by one with FP32 checkpoints; batched = all shots per
@@ -430,20 +430,29 @@ def run_fwi(nshots, nt, k, dev):
         sv.set_sources(w.src)
         sv.set_receivers(base.rec)
         solvers.append(sv)
-    b = fw.Batch(solvers)
+    # groups of `group` shots per batch keep the FP16 snapshots within HBM
+    groups = [list(range(i, min(i + group, nshots))) for i in range(0, nshots, group)]
+    batches = [fw.Batch([solvers[i] for i in g]) for g in groups]
     recs = [torch.empty((nt, nrec), device=dev) for _ in shots]
-    b.forward_ckpt(qs, k, "f16", recs=recs)   # allocation and graph capture, untimed
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    b.forward_ckpt(qs, k, "f16", recs=recs)
-    grads = b.gradient(recs, dobs)
     g_batch = torch.zeros_like(g_plain)
-    for g in grads:
-        g_batch += g.double()
+    b0 = batches[0]
+    b0.forward_ckpt([qs[i] for i in groups[0]], k, "f16", recs=[recs[i] for i in groups[0]])
+    torch.cuda.synchronize(dev)   # allocation and graph capture of one group, untimed
+    t0 = time.perf_counter()
+    for g, b in zip(groups, batches):
+        b.forward_ckpt([qs[i] for i in g], k, "f16", recs=[recs[i] for i in g])
+        grads = b.gradient([recs[i] for i in g], [dobs[i] for i in g])
+        for gr in grads:
+            g_batch += gr.double()
+        if len(groups) > 1:   # release this group's checkpoints before the next group
+            b.close()
+            for i in g:
+                solvers[i].close()
     torch.cuda.synchronize(dev)
     t_batch = time.perf_counter() - t0
     diff = float(torch.linalg.vector_norm(g_batch - g_plain) / torch.linalg.vector_norm(g_plain))
-    b.close()
+    for b in batches:
+        b.close()
     for sv in solvers:
         sv.close()
     return {"workload": f"{nshots} shots, 256^3 (336^3 computational), SO8, {nt} steps, "
@@ -452,13 +461,133 @@ def run_fwi(nshots, nt, k, dev):
             "grad_rel_l2_batched_fp16_vs_plain_fp32": diff}
 
 
+def run_so16(args, dev):
+    """512^3 SO16 forward (592^3 computational), 2000 steps, FP32: GPts/s."""
+    import torch
+    from paper_1609_03361_gb300 import fdwave as fw
+    from paper_1609_03361_gb300 import workloads as W
+    w = W.config_3d(512, 12.5, 16, args.nt if args.nt != 1000 else 2000)
+    w.dt = W.choose_dt(fw.fdw_dt_max(3, w.spacing, 16, w.vmax))
+    pts = int(np.prod(w.comp_shape))
+    s = fw.Solver(w.shape, w.spacing, 16, w.nbl, w.dt, w.nt, w.vmax, device=dev.index or 0)
+    s.set_model(torch.from_numpy(w.m.astype(np.float32)).to(dev))
+    s.set_sources(w.src)
+    s.set_receivers(w.rec)
+    q = torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev)
+    rec = torch.empty((w.nt, w.rec.shape[0]), device=dev)
+    s.autotune(3)
+    for _ in range(args.warmup):
+        s.forward(q, rec)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        s.forward(q, rec)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    s.sync()
+    g = pts * (w.nt - 1) / (ms * 1e-3) / 1e9
+    peak, _ = measured_peaks()
+    line = {"metric": "GPts/s (SO-16 3D FP32 forward)", "value": g, "unit": "GPts/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"3D acoustic forward 512^3 (592^3 computational), SO16, "
+                                   f"{w.nt} steps", "tiling": s.tiling()},
+            "roofline": {"bound": "hbm", "achieved": g * B_ALG, "peak": peak, "unit": "GB/s",
+                         "frac": g * B_ALG / peak}}
+    s.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_precision(args, dev):
+    """Errors of the 16-bit model and snapshot storage.  Model: SO16 with the
+    512^3 recipe, traces of FP32 / FP16 / BF16 model storage against the FP64
+    oracle on a 128^3 grid (all steps) and against each other on the full
+    512^3 grid.  Snapshots: SO8 gradients with FP32 / FP16 / BF16 checkpoints
+    against the FP64 oracle gradient on a 64^3 grid, 400 steps."""
+    import torch
+    import oracle
+    from paper_1609_03361_gb300 import fdwave as fw
+    from paper_1609_03361_gb300 import workloads as W
+
+    def rel(a, b):
+        a = np.asarray(a, np.float64)
+        b = np.asarray(b, np.float64)
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    out = {}
+    # (1) model storage vs FP64 oracle, reduced grid, SO16
+    n, nt = 128, 600
+    w = W.config_3d(n, 12.5, 16, nt, nrec_side=32)
+    w.dt = W.choose_dt(fw.fdw_dt_max(3, w.spacing, 16, w.vmax))
+    st = oracle.Setup(w.shape, w.spacing, 16, w.nbl, w.dt, nt)
+    q = w.wavelet().astype(np.float32)[:, None]
+    ref = oracle.forward(st, oracle.extend_model(st, w.m.astype(np.float32).astype(np.float64)),
+                         oracle.damping(st, w.vmax), w.src, q.astype(np.float64), w.rec)
+    s = fw.Solver(w.shape, w.spacing, 16, w.nbl, w.dt, nt, w.vmax, device=dev.index or 0)
+    s.set_sources(w.src)
+    s.set_receivers(w.rec)
+    res = {}
+    for mt in ("f32", "f16", "bf16"):
+        s.set_model(w.m.astype(np.float32), "physical", mt)
+        res[mt] = rel(s.forward(q), ref)
+    s.close()
+    out["model_storage_vs_fp64_oracle"] = {"workload": f"{n}^3 SO16, {nt} steps, 1024 receivers",
+                                           "rel_l2_traces": res}
+    # (2) model storage on the full 512^3 grid, against FP32 storage
+    w = W.config_3d(512, 12.5, 16, 2000)
+    w.dt = W.choose_dt(fw.fdw_dt_max(3, w.spacing, 16, w.vmax))
+    s = fw.Solver(w.shape, w.spacing, 16, w.nbl, w.dt, w.nt, w.vmax, device=dev.index or 0)
+    s.set_sources(w.src)
+    s.set_receivers(w.rec)
+    qd = torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev)
+    md = torch.from_numpy(w.m.astype(np.float32)).to(dev)
+    tr = {}
+    for mt in ("f32", "f16", "bf16"):
+        s.set_model(md, "physical", mt)
+        tr[mt] = s.forward(qd).cpu().numpy()
+    s.close()
+    out["model_storage_full_grid_vs_fp32"] = {
+        "workload": "512^3 (592^3 computational) SO16, 2000 steps, 16384 receivers",
+        "rel_l2_traces": {mt: rel(tr[mt], tr["f32"]) for mt in ("f16", "bf16")}}
+    # (3) snapshot storage vs the FP64 oracle gradient
+    n, nt = 64, 400
+    w = W.config_3d(n, 12.5, 8, nt, nrec_side=32)
+    w.dt = W.choose_dt(fw.fdw_dt_max(3, w.spacing, 8, w.vmax))
+    st = oracle.Setup(w.shape, w.spacing, 8, w.nbl, w.dt, nt)
+    M = oracle.extend_model(st, w.m.astype(np.float32).astype(np.float64))
+    eta = oracle.damping(st, w.vmax)
+    q = w.wavelet().astype(np.float32)[:, None]
+    d = oracle.forward(st, oracle.extend_model(st, (1 / W.anomaly(w.velocity) ** 2)),
+                       eta, w.src, q.astype(np.float64), w.rec)
+    s = fw.Solver(w.shape, w.spacing, 8, w.nbl, w.dt, nt, w.vmax, device=dev.index or 0)
+    s.set_model(w.m.astype(np.float32))
+    s.set_sources(w.src)
+    s.set_receivers(w.rec)
+    d32 = d.astype(np.float32)
+    gres = {}
+    for stype in ("f32", "f16", "bf16"):
+        rec = s.forward_ckpt(q, 10, stype)
+        g = s.gradient(rec, d32)
+        if stype == "f32":
+            gref = oracle.gradient(st, M, eta, w.src, q.astype(np.float64), w.rec,
+                                   rec.astype(np.float64) - d)
+        gres[stype] = rel(g, gref)
+    s.close()
+    out["snapshot_storage_vs_fp64_oracle_gradient"] = {
+        "workload": f"{n}^3 SO8, {nt} steps, checkpoints every 10 steps, +5% anomaly data",
+        "rel_l2_gradient": gres}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--workload", default="forward", choices=["forward"])
+    ap.add_argument("--workload", default="forward", choices=["forward", "so16", "precision"])
     ap.add_argument("--nt", type=int, default=1000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -477,6 +606,13 @@ def main():
         run_reference(args, world, rank)
         return
     world, rank, local = dist_init()
+    if args.workload != "forward":
+        import torch
+        dev = torch.device("cuda", local)
+        torch.cuda.set_device(dev)
+        if rank == 0:
+            (run_so16 if args.workload == "so16" else run_precision)(args, dev)
+        return
     run_forward(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
