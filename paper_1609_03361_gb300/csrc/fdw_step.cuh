@@ -65,13 +65,12 @@ __device__ __forceinline__ void release_stage(uint32_t empty_bar, int lane) {
 }
 
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort) {
-#pragma unroll 1
-  for (int i = 0; i < 32; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_try_wait(bar, parity)) return true;
   long long t0 = clock64();
 #pragma unroll 1
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    // parked in hardware (up to 20 us per try) rather than spinning
+    if (mbar_try_wait_suspend(bar, parity, 20000u)) return true;
     if (*abort) return false;
     if (clock64() - t0 > kWaitBudget) return false;
   }
