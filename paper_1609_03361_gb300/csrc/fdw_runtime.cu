@@ -295,7 +295,7 @@ struct Plan {
     const void* fn;
     int grid, threads;
     size_t smem;
-    int stage_bytes, off_p, off_m, off_f, off_e;
+    int stage_bytes, off_p, off_m, off_f, off_a, off_e;
   };
   std::map<std::tuple<int, int, int, int, int, int>, LaunchInfo> launch_cache;
   std::vector<double> weights;       // unscaled second-derivative weights c_0..c_r
@@ -435,7 +435,7 @@ static void compute_points(fdw_ctx* c, PointSet& ps, int n, const double* xyz) {
 // ---------------------------------------------------------------- plan
 
 struct StageLayout {
-  int off_p, off_m, off_f, off_e, bytes;
+  int off_p, off_m, off_f, off_a, off_e, bytes;
 };
 
 static int round128(int x) { return (x + 127) & ~127; }
@@ -451,6 +451,8 @@ static StageLayout stage_layout(int r, int tile, int mt_bytes, bool grad, bool e
   L.off_m = off;
   off += round128(TY * kTZ * mt_bytes);
   L.off_f = off;
+  if (grad) off += round128(TY * kTZ * 4);
+  L.off_a = off;
   if (grad) off += round128(TY * kTZ * 4);
   L.off_e = off;
   if (etaf) off += round128(TY * kTZ * 4);
@@ -651,6 +653,8 @@ static ShotDesc make_desc(const Plan& pl, fdw_ctx* c, int role) {
     d.fwd = c->seg;
     d.fslot = c->slot;
     d.acc = c->acc;
+    make_map(&d.tm_a, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->acc, c->nx, c->ny, c->nz, c->nzp, 0,
+             c->slot, kTZ, TY);
   }
   if (c->use_etaf) {
     make_map(&d.tm_e, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->etaf, c->nx, c->ny, c->nz, c->nzp, 0,
@@ -741,6 +745,7 @@ static const Plan::LaunchInfo& launch_info(Plan& pl, bool grad) {
   li.off_p = L.off_p;
   li.off_m = L.off_m;
   li.off_f = L.off_f;
+  li.off_a = L.off_a;
   li.off_e = L.off_e;
   return pl.launch_cache.emplace(key, li).first->second;
 }
@@ -775,6 +780,7 @@ static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s) {
   P.off_p = li.off_p;
   P.off_m = li.off_m;
   P.off_f = li.off_f;
+  P.off_a = li.off_a;
   P.off_e = li.off_e;
   const double dt = c0->dt;
   P.dt2 = (float)(dt * dt);

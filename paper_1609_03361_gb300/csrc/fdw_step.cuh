@@ -239,8 +239,10 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
       float val[NY][kVZ];
       float d2t[NY][kVZ];
       float4 fw[NY];
+      float4 aw[NY];
       (void)d2t;
       (void)fw;
+      (void)aw;
 #pragma unroll
       for (int i = 0; i < R; ++i) {
         yr[i] = lds4(U + (r0 + i) * ZW + R4 + zl);
@@ -287,7 +289,10 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
           val[j][v] = __fdividef(num, 1.f + es);
           if (GRAD) d2t[j][v] = val[j][v] - 2.f * c + prev;  // second time difference of lambda
         }
-        if (GRAD) fw[j] = lds4(reinterpret_cast<const float*>(sb + P.off_f) + li);
+        if (GRAD) {
+          fw[j] = lds4(reinterpret_cast<const float*>(sb + P.off_f) + li);
+          aw[j] = lds4(reinterpret_cast<const float*>(sb + P.off_a) + li);
+        }
       }
       // every read of the staged planes is done: hand them back before the
       // global stores, which only read registers
@@ -301,7 +306,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
           *reinterpret_cast<float4*>(uo + off) =
               make_float4(val[j][0], val[j][1], val[j][2], val[j][3]);
           if (GRAD) {
-            float4 a = *reinterpret_cast<const float4*>(acc + off);
+            float4 a = aw[j];  // the accumulator tile was staged with the plane
             a.x = fmaf(fw[j].x, d2t[j][0], a.x);
             a.y = fmaf(fw[j].y, d2t[j][1], a.y);
             a.z = fmaf(fw[j].z, d2t[j][2], a.z);
@@ -371,7 +376,7 @@ step_kernel(const __grid_constant__ StepParams P) {
         const Unit un = P.units[u];
         const ShotDesc* d = P.shots + un.shot;
         const uint32_t bytes_in = TY * TZ * 4 + TY * TZ * (d->mtype == kF32 ? 4 : 2) +
-                                  (GRAD ? TY * TZ * 4 : 0) +
+                                  (GRAD ? 2 * TY * TZ * 4 : 0) +
                                   ((P.flags & kEtaField) ? TY * TZ * 4 : 0);
         for (int p = un.x0 - R; p < un.x1 + R; ++p) {
           const uint32_t full = full0 + 8 * c.stage, empty = empty0 + 8 * c.stage;
@@ -387,7 +392,10 @@ step_kernel(const __grid_constant__ StepParams P) {
           if (inner) {
             tma_load_4d(sb + P.off_p, &d->tm_uc, un.z0, un.y0, p, P.prev, full);
             tma_load_3d(sb + P.off_m, &d->tm_m, un.z0, un.y0, p, full);
-            if (GRAD) tma_load_4d(sb + P.off_f, &d->tm_f, un.z0, un.y0, p, P.fslot, full);
+            if (GRAD) {
+              tma_load_4d(sb + P.off_f, &d->tm_f, un.z0, un.y0, p, P.fslot, full);
+              tma_load_3d(sb + P.off_a, &d->tm_a, un.z0, un.y0, p, full);
+            }
             if (P.flags & kEtaField) tma_load_3d(sb + P.off_e, &d->tm_e, un.z0, un.y0, p, full);
           }
           ++issued;

@@ -36,6 +36,7 @@ struct alignas(128) ShotDesc {
   CUtensorMap tm_m;    // model s = 1/m [nx][ny][nzp] (f32 / f16 / bf16), centre box (TZ, TY, 1)
   CUtensorMap tm_f;    // forward-wavefield slots (gradient), centre box (TZ, TY, 1, 1)
   CUtensorMap tm_e;    // damping field (eta*dt/2) [nx][ny][nzp] f32, centre box (optional)
+  CUtensorMap tm_a;    // gradient accumulator [nx][ny][nzp] f32, centre box (gradient)
   float* u;            // base of the wavefield slots
   long long uslot;     // floats per slot
   const float* fwd;    // forward-wavefield slots (adjoint + gradient)
@@ -94,6 +95,7 @@ struct StepParams {
   int stages;          // pipeline depth
   int stage_bytes;     // bytes of one pipeline stage
   int off_p, off_m, off_f, off_e;  // byte offsets inside a stage
+  int off_a;           // byte offset of the gradient-accumulator tile (gradient)
   float dt2;           // dt^2
   float csum;          // sum of the centre weights over the axes
   float w[3][kMaxR + 1];  // dt^2 c_k / h_a^2, k = 0..r (k = 0 unused; see csum)
