@@ -10,6 +10,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "fdw_internal.h"
 
 namespace fdw {
@@ -87,15 +89,21 @@ __global__ void eta_field_kernel(const float* in, float scale, float* out, Geom 
     out[pitched(g, i)] = in[i] * scale;
 }
 
+// Snapshot kernels work on whole pitched fields, four floats per access: the
+// padding past nz is zero in every wavefield, so it packs and unpacks to zero.
+
 // max(|a|, |b|) over a pair of pitched fields, per shot (blockIdx.y).
 __global__ void absmax_kernel(const AuxShot* shots) {
   const AuxShot& s = shots[blockIdx.y];
-  const long long n = dense_points(s.g);
+  const long long n4 = s.n / 4;
+  const float4* a = reinterpret_cast<const float4*>(s.a);
+  const float4* b = reinterpret_cast<const float4*>(s.b);
   float m = 0.f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long o = pitched(s.g, i);
-    m = fmaxf(m, fmaxf(fabsf(s.a[o]), fabsf(s.b[o])));
+    const float4 x = a[i], y = b[i];
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(y.x), fabsf(y.y)), fmaxf(fabsf(y.z), fabsf(y.w))));
   }
   for (int k = 16; k > 0; k >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, k));
   __shared__ float red[kThreads / 32];
@@ -114,53 +122,82 @@ __device__ inline float snap_scale(const unsigned int* amax, int stype) {
   return m > 0.f ? 16384.f / m : 1.f;
 }
 
-__global__ void pack_kernel(const AuxShot* shots, int stype) {
+template <typename H>
+__device__ inline uint2 to16x4(float4 v, float sc);
+template <>
+__device__ inline uint2 to16x4<__half>(float4 v, float sc) {
+  const __half2 lo = __floats2half2_rn(v.x * sc, v.y * sc);
+  const __half2 hi = __floats2half2_rn(v.z * sc, v.w * sc);
+  return make_uint2(*reinterpret_cast<const unsigned*>(&lo), *reinterpret_cast<const unsigned*>(&hi));
+}
+template <>
+__device__ inline uint2 to16x4<__nv_bfloat16>(float4 v, float sc) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x * sc, v.y * sc);
+  const __nv_bfloat162 hi = __floats2bfloat162_rn(v.z * sc, v.w * sc);
+  return make_uint2(*reinterpret_cast<const unsigned*>(&lo), *reinterpret_cast<const unsigned*>(&hi));
+}
+
+template <typename H>
+__device__ inline float4 from16x4(uint2 r, float inv);
+template <>
+__device__ inline float4 from16x4<__half>(uint2 r, float inv) {
+  const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+  const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+  return make_float4(lo.x * inv, lo.y * inv, hi.x * inv, hi.y * inv);
+}
+template <>
+__device__ inline float4 from16x4<__nv_bfloat16>(uint2 r, float inv) {
+  const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.x));
+  const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.y));
+  return make_float4(lo.x * inv, lo.y * inv, hi.x * inv, hi.y * inv);
+}
+
+template <typename H>
+__global__ void pack16_kernel(const AuxShot* shots) {
   const AuxShot& s = shots[blockIdx.y];
-  const long long n = dense_points(s.g);
-  const float sc = snap_scale(s.amax, stype);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+  const long long n4 = s.n / 4;
+  const float sc = snap_scale(s.amax, kF16);
+  const float4* a = reinterpret_cast<const float4*>(s.a);
+  const float4* b = reinterpret_cast<const float4*>(s.b);
+  uint2* h = static_cast<uint2*>(s.snap);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long o = pitched(s.g, i);
-    const float a = s.a[o], b = s.b[o];
-    if (stype == kF16) {
-      __half* h = static_cast<__half*>(s.snap);
-      h[i] = __float2half_rn(a * sc);
-      h[n + i] = __float2half_rn(b * sc);
-    } else if (stype == kBF16) {
-      __nv_bfloat16* h = static_cast<__nv_bfloat16*>(s.snap);
-      h[i] = __float2bfloat16_rn(a * sc);
-      h[n + i] = __float2bfloat16_rn(b * sc);
-    } else {
-      float* h = static_cast<float*>(s.snap);
-      h[i] = a;
-      h[n + i] = b;
-    }
+    h[i] = to16x4<H>(a[i], sc);
+    h[n4 + i] = to16x4<H>(b[i], sc);
   }
 }
 
-__global__ void unpack_kernel(const AuxShot* shots, int stype) {
+template <typename H>
+__global__ void unpack16_kernel(const AuxShot* shots) {
   const AuxShot& s = shots[blockIdx.y];
-  const long long n = dense_points(s.g);
-  const float inv = 1.f / snap_scale(s.amax, stype);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+  const long long n4 = s.n / 4;
+  const float inv = 1.f / snap_scale(s.amax, kF16);
+  float4* a = reinterpret_cast<float4*>(s.a);
+  float4* b = reinterpret_cast<float4*>(s.b);
+  const uint2* h = static_cast<const uint2*>(s.snap);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long o = pitched(s.g, i);
-    float a, b;
-    if (stype == kF16) {
-      const __half* h = static_cast<const __half*>(s.snap);
-      a = __half2float(h[i]) * inv;
-      b = __half2float(h[n + i]) * inv;
-    } else if (stype == kBF16) {
-      const __nv_bfloat16* h = static_cast<const __nv_bfloat16*>(s.snap);
-      a = __bfloat162float(h[i]) * inv;
-      b = __bfloat162float(h[n + i]) * inv;
+    a[i] = from16x4<H>(h[i], inv);
+    b[i] = from16x4<H>(h[n4 + i], inv);
+  }
+}
+
+// FP32 snapshots: plain copies in either direction (dir 0: fields -> snapshot).
+__global__ void copy32_kernel(const AuxShot* shots, int dir) {
+  const AuxShot& s = shots[blockIdx.y];
+  const long long n4 = s.n / 4;
+  float4* a = reinterpret_cast<float4*>(s.a);
+  float4* b = reinterpret_cast<float4*>(s.b);
+  float4* h = static_cast<float4*>(s.snap);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (dir == 0) {
+      h[i] = a[i];
+      h[n4 + i] = b[i];
     } else {
-      const float* h = static_cast<const float*>(s.snap);
-      a = h[i];
-      b = h[n + i];
+      a[i] = h[i];
+      b[i] = h[n4 + i];
     }
-    s.a[o] = a;
-    s.b[o] = b;
   }
 }
 
@@ -232,23 +269,34 @@ cudaError_t launch_eta_field(const float* in, float scale, float* out, Geom g, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_absmax(const AuxShot* shots, int nshots, long long maxpts, cudaStream_t s) {
-  dim3 grid(blocks_for(maxpts), nshots);
-  absmax_kernel<<<grid, kThreads, 0, s>>>(shots);
+// Grid of a snapshot kernel: float4 units of the largest field, at most 8
+// blocks of 256 threads per SM.
+static dim3 snap_grid(long long maxn, int nshots) {
+  long long b = (maxn / 4 + kThreads - 1) / kThreads;
+  b = std::max(1LL, std::min(b, 152LL * 8));
+  return dim3((unsigned)b, (unsigned)nshots);
+}
+
+cudaError_t launch_absmax(const AuxShot* shots, int nshots, long long maxn, cudaStream_t s) {
+  absmax_kernel<<<snap_grid(maxn, nshots), kThreads, 0, s>>>(shots);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const AuxShot* shots, int nshots, long long maxpts, int stype,
+cudaError_t launch_pack(const AuxShot* shots, int nshots, long long maxn, int stype,
                         cudaStream_t s) {
-  dim3 grid(blocks_for(maxpts), nshots);
-  pack_kernel<<<grid, kThreads, 0, s>>>(shots, stype);
+  const dim3 g = snap_grid(maxn, nshots);
+  if (stype == kF16) pack16_kernel<__half><<<g, kThreads, 0, s>>>(shots);
+  else if (stype == kBF16) pack16_kernel<__nv_bfloat16><<<g, kThreads, 0, s>>>(shots);
+  else copy32_kernel<<<g, kThreads, 0, s>>>(shots, 0);
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(const AuxShot* shots, int nshots, long long maxpts, int stype,
+cudaError_t launch_unpack(const AuxShot* shots, int nshots, long long maxn, int stype,
                           cudaStream_t s) {
-  dim3 grid(blocks_for(maxpts), nshots);
-  unpack_kernel<<<grid, kThreads, 0, s>>>(shots, stype);
+  const dim3 g = snap_grid(maxn, nshots);
+  if (stype == kF16) unpack16_kernel<__half><<<g, kThreads, 0, s>>>(shots);
+  else if (stype == kBF16) unpack16_kernel<__nv_bfloat16><<<g, kThreads, 0, s>>>(shots);
+  else copy32_kernel<<<g, kThreads, 0, s>>>(shots, 1);
   return cudaGetLastError();
 }
 

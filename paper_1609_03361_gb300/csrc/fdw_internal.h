@@ -36,10 +36,10 @@ struct Geom {
 
 // Per-shot descriptor of the auxiliary (per-call, not per-step) kernels.
 struct AuxShot {
-  Geom g;
+  long long n;          // floats per pitched field (a multiple of 32)
   float* a;             // first field (slot base)
   float* b;             // second field
-  void* snap;           // snapshot pair base (two compact fields)
+  void* snap;           // snapshot pair base: two pitched fields of n elements
   unsigned int* amax;   // absolute maximum of the pair, float bits
 };
 
@@ -48,10 +48,11 @@ cudaError_t launch_sample(const ShotDesc* shots, int nshots, int maxpts, int slo
 cudaError_t launch_model(const float* in, int layout, int phys_x, int phys_y, int phys_z,
                          int nbl, int ndim, void* out, int mtype, Geom g, cudaStream_t s);
 cudaError_t launch_eta_field(const float* in, float scale, float* out, Geom g, cudaStream_t s);
-cudaError_t launch_absmax(const AuxShot* shots, int nshots, long long maxpts, cudaStream_t s);
-cudaError_t launch_pack(const AuxShot* shots, int nshots, long long maxpts, int stype,
+// maxn: the largest field (floats per pitched slot) of the shots
+cudaError_t launch_absmax(const AuxShot* shots, int nshots, long long maxn, cudaStream_t s);
+cudaError_t launch_pack(const AuxShot* shots, int nshots, long long maxn, int stype,
                         cudaStream_t s);
-cudaError_t launch_unpack(const AuxShot* shots, int nshots, long long maxpts, int stype,
+cudaError_t launch_unpack(const AuxShot* shots, int nshots, long long maxn, int stype,
                           cudaStream_t s);
 cudaError_t launch_grad_out(const float* acc, Geom g, float scale, float* out, int layout,
                             int nbl, int ndim, int phys_x, int phys_y, int phys_z,

@@ -293,7 +293,7 @@ struct Plan {
   std::vector<int> built_versions;   // points/buffers versions the lists and maps were built for
   struct LaunchInfo {
     const void* fn;
-    int grid, threads;
+    int grid, threads, stages;
     size_t smem;
     int stage_bytes, off_p, off_m, off_f, off_a, off_e;
   };
@@ -303,6 +303,8 @@ struct Plan {
   int max_rec = 0, max_src = 0;
   bool test_stall = false;  // FDW_TEST_STALL: make every step's waits run out (tests only)
   long long max_points = 0;
+  long long max_slot = 0;            // floats per pitched field, largest shot
+  int grad_stages = 0, grad_stages_tile = -1;  // pipeline depth of the gradient step
 
   void clear_graphs() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
@@ -564,10 +566,12 @@ static void build_lists(Plan& pl) {
   };
   pl.max_rec = pl.max_src = 0;
   pl.max_points = 0;
+  pl.max_slot = 0;
   for (auto* c : pl.shots) {
     pl.max_rec = std::max(pl.max_rec, c->rec.n);
     pl.max_src = std::max(pl.max_src, c->src.n);
     pl.max_points = std::max(pl.max_points, (long long)c->nx * c->ny * c->nz);
+    pl.max_slot = std::max(pl.max_slot, c->slot);
   }
   for (int role = 0; role < kNumRoles; ++role) {
     RoleLists& L = pl.lists[role];
@@ -663,6 +667,7 @@ static ShotDesc make_desc(const Plan& pl, fdw_ctx* c, int role) {
   }
   d.m = c->m;
   d.eta = c->eta;
+  if (role == kRoleFwd) d.amax = c->amax;
   const PointSet& sp = (role == kRoleAdj) ? c->src : c->rec;
   if (role != kRoleRec) {
     d.pt_base = sp.d_base;
@@ -717,24 +722,52 @@ static void upload_desc(Plan& pl, int role, cudaStream_t s) {
 
 // ---------------------------------------------------------------- launches
 
+// Pipeline depth of the gradient step, whose stages carry two more tiles than
+// the forward step's: the deepest pipeline among those with the most resident
+// CTAs per SM (more consumer warps hide more latency than a deeper prefetch).
+static int grad_stages(Plan& pl) {
+  if (pl.grad_stages_tile == pl.tile) return pl.grad_stages;
+  const StageLayout L = stage_layout(pl.r, pl.tile, msize(plan_mtype(pl)), true, plan_etaf(pl));
+  const void* fn = step_fn(pl.r, pl.tile, true);
+  const int threads = (kTiles[pl.tile].warps + 1) * 32;
+  const int cap = device_smem_optin(pl.device) - 1024;
+  int best = pl.r + 2, best_nb = -1;
+  for (int st = pl.r + 2; st <= 2 * pl.r + 8 && (int)smem_bytes(L, st) <= cap; ++st) {
+    const size_t smem = smem_bytes(L, st);
+    configure_kernel(fn, smem);
+    int nb = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem));
+    if (nb >= best_nb) {
+      best_nb = nb;
+      best = st;
+    }
+  }
+  pl.grad_stages = best;
+  pl.grad_stages_tile = pl.tile;
+  return best;
+}
+
 struct StepArgs {
   int role;
   int cur, prev, out, fslot;
   int inj_row, smp_row;
   int flags;
   bool grad;
+  int amax_slot = 0;
 };
 
 static const Plan::LaunchInfo& launch_info(Plan& pl, bool grad) {
   const bool etaf = plan_etaf(pl);
   const int mt = plan_mtype(pl);
   const int nunits = (int)pl.units.size();
-  auto key = std::make_tuple(pl.tile, pl.stages, (int)grad, (int)etaf, mt, nunits);
+  const int stages = grad ? grad_stages(pl) : pl.stages;
+  auto key = std::make_tuple(pl.tile, stages, (int)grad, (int)etaf, mt, nunits);
   auto it = pl.launch_cache.find(key);
   if (it != pl.launch_cache.end()) return it->second;
   const StageLayout L = stage_layout(pl.r, pl.tile, msize(mt), grad, etaf);
   Plan::LaunchInfo li;
-  li.smem = smem_bytes(L, pl.stages);
+  li.smem = smem_bytes(L, stages);
+  li.stages = stages;
   li.fn = step_fn(pl.r, pl.tile, grad);
   configure_kernel(li.fn, li.smem);
   int nb = 0;
@@ -775,7 +808,8 @@ static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s) {
   P.prev = a.prev;
   P.out = a.out;
   P.fslot = a.fslot;
-  P.stages = pl.stages;
+  P.amax_slot = a.amax_slot;
+  P.stages = li.stages;
   P.stage_bytes = li.stage_bytes;
   P.off_p = li.off_p;
   P.off_m = li.off_m;
@@ -845,14 +879,27 @@ static void forward_body(Plan& pl, int k, int stype, cudaStream_t s) {
   const int nsnap = k > 0 ? (nt - 1) / k : 0;
   if (nsnap > 0)
     for (auto* c : pl.shots) CK(cudaMemsetAsync(c->amax, 0, sizeof(unsigned) * nsnap, s));
+  // 16-bit snapshots need max |u| of the pair: with k >= 2 the two steps that
+  // produce u^{jk-1} and u^{jk} fold it into amax[j-1] as they go; k = 1 (each
+  // field in two pairs) takes a separate pass
+  const bool scaled = stype != kF32;
+  const bool fused_max = scaled && k >= 2;
   for (int n = 0; n + 1 < nt; ++n) {
     StepArgs a{kRoleFwd, n & 1, (n + 1) & 1, (n + 1) & 1, 0, n, n, flags_base, false};
+    if (fused_max) {
+      const int j = (n + 2) / k;  // u^{n+1} is the first or second field of pair j
+      if (((n + 1) % k == 0 || (n + 2) % k == 0) && j >= 1 && j <= nsnap) {
+        a.flags |= kAbsMax;
+        a.amax_slot = j - 1;
+      }
+    }
     launch_step(pl, a, s);
     if (k > 0 && (n + 1) % k == 0 && (n + 1) / k <= nsnap) {
       const int j = (n + 1) / k;  // snapshot j holds (u^{jk}, u^{jk-1})
       const size_t ns = pl.shots.size();
-      CK(launch_absmax(pl.d_pack + (size_t)(j - 1) * ns, (int)ns, pl.max_points, s));
-      CK(launch_pack(pl.d_pack + (size_t)(j - 1) * ns, (int)ns, pl.max_points, stype, s));
+      if (scaled && !fused_max)
+        CK(launch_absmax(pl.d_pack + (size_t)(j - 1) * ns, (int)ns, pl.max_slot, s));
+      CK(launch_pack(pl.d_pack + (size_t)(j - 1) * ns, (int)ns, pl.max_slot, stype, s));
     }
   }
   if (pl.max_rec > 0)
@@ -888,7 +935,7 @@ static void gradient_body(Plan& pl, int k, int stype, bool diff, cudaStream_t s)
     if (j == 0) {
       for (auto* c : pl.shots) CK(cudaMemsetAsync(c->seg, 0, sizeof(float) * 2 * c->slot, s));
     } else {
-      CK(launch_unpack(pl.d_unpack + (size_t)(j - 1) * ns, (int)ns, pl.max_points, stype, s));
+      CK(launch_unpack(pl.d_unpack + (size_t)(j - 1) * ns, (int)ns, pl.max_slot, stype, s));
     }
     // recompute u^{a0+1} .. u^{b0-1}; slot i holds u^{a0-1+i}
     for (int n = a0; n <= b0 - 2; ++n) {
@@ -906,12 +953,11 @@ static void gradient_body(Plan& pl, int k, int stype, bool diff, cudaStream_t s)
 // Checkpoint buffers of a context for k and snapshot type.
 static void ensure_ckpt(fdw_ctx* c, int k, int stype) {
   const int nsnap = (c->nt - 1) / k;
-  const long long pts = (long long)c->nx * c->ny * c->nz;
   if (c->ckpt_k != k || c->snap_type != stype || !c->seg) {
     dfree(c->snaps); dfree(c->amax); dfree(c->seg);
     c->snaps = nullptr; c->amax = nullptr; c->seg = nullptr;
     c->have_ckpt = false;
-    const size_t per = (size_t)pts * 2 * msize(stype);
+    const size_t per = (size_t)c->slot * 2 * msize(stype);  // pitched pair
     c->snaps = dalloc<unsigned char>(std::max<size_t>(1, per * (size_t)nsnap));
     c->amax = dalloc<unsigned int>(std::max(1, nsnap));
     c->seg_slots = k + 1;
@@ -944,10 +990,9 @@ static void ensure_aux(Plan& pl) {
   for (int j = 1; j <= nsnap; ++j)
     for (size_t s = 0; s < ns; ++s) {
       fdw_ctx* c = pl.shots[s];
-      const long long pts = (long long)c->nx * c->ny * c->nz;
-      const size_t per = (size_t)pts * 2 * msize(c->snap_type);
+      const size_t per = (size_t)c->slot * 2 * msize(c->snap_type);
       AuxShot a;
-      a.g = Geom{c->nx, c->ny, c->nz, c->nzp};
+      a.n = c->slot;
       a.snap = static_cast<unsigned char*>(c->snaps) + per * (size_t)(j - 1);
       a.amax = c->amax + (j - 1);
       a.a = c->u + (size_t)((j * k) & 1) * c->slot;       // u^{jk}

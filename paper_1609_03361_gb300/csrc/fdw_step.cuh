@@ -139,7 +139,8 @@ template <int R, int NY, int BY, bool GRAD, bool XU, typename MT>
 __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, const ShotDesc* d,
                                          int u, const unsigned char* smem, uint32_t full0,
                                          uint32_t empty0, Cursor& ca, Cursor& cb,
-                                         volatile int* abort_flag, int lane, const Lanes L) {
+                                         volatile int* abort_flag, int lane, const Lanes L,
+                                         float& tmax) {
   constexpr int TZ = kTZ;
   constexpr int R4 = Halo<R>::R4;
   constexpr int ZW = Halo<R>::ZW;
@@ -149,6 +150,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
   const int S = P.stages;
   const int ny = d->ny, nz = d->nz, nzp = d->nzp;
   const bool etaf = (P.flags & kEtaField) != 0;
+  const bool amx = (P.flags & kAbsMax) != 0;
   const int r0 = L.r0, zl = L.zl;
   const int z = un.z0 + zl;
   const bool zin = z < nz;
@@ -299,6 +301,12 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
       release_stage(empty0 + 8 * cb.stage, lane);
       if (x + R >= un.x1) release_stage(empty0 + 8 * ahead_stage, lane);
       cb.next(S);
+      if (amx) {  // points past the grid compute to zero and do not move the maximum
+#pragma unroll
+        for (int j = 0; j < NY; ++j)
+#pragma unroll
+          for (int v = 0; v < kVZ; ++v) tmax = fmaxf(tmax, fabsf(val[j][v]));
+      }
 #pragma unroll
       for (int j = 0; j < NY; ++j) {
         if (rowok[j]) {
@@ -413,6 +421,7 @@ step_kernel(const __grid_constant__ StepParams P) {
     Cursor cb{0, 0u};   // compute cursor: the plane being updated
     uint32_t tail_phase = 0u;
     const int tid = threadIdx.x;
+    float tmax = 0.f;  // max |u^{n+1}| of the thread's points in the current unit (kAbsMax)
     bool ok = true;
     for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
       const Unit un = P.units[u];
@@ -420,13 +429,13 @@ step_kernel(const __grid_constant__ StepParams P) {
       const int mtype = d->mtype;
       if (mtype == kF16)
         ok = run_unit<R, NY, BY, GRAD, XU, __half>(P, un, d, u, smem, full0, empty0, ca, cb,
-                                               abort_flag, lane, L);
+                                               abort_flag, lane, L, tmax);
       else if (mtype == kBF16)
         ok = run_unit<R, NY, BY, GRAD, XU, __nv_bfloat16>(P, un, d, u, smem, full0, empty0, ca, cb,
-                                                      abort_flag, lane, L);
+                                                      abort_flag, lane, L, tmax);
       else
         ok = run_unit<R, NY, BY, GRAD, XU, float>(P, un, d, u, smem, full0, empty0, ca, cb,
-                                              abort_flag, lane, L);
+                                              abort_flag, lane, L, tmax);
       if (!ok) break;
 
       // ---- unit tail: injection into u^{n+1} and sampling of u^n ----
@@ -455,9 +464,21 @@ step_kernel(const __grid_constant__ StepParams P) {
                                : d->eta[nd.x] + d->eta[nx + nd.y] + d->eta[nx + ny + nd.z];
           // dt^2 q / (m + eta dt/2) with s = 1/m
           const float delta = P.dt2 * sum * s / (1.f + e * s);
-          uo[off] += delta;
+          const float nv = uo[off] + delta;
+          uo[off] = nv;
+          tmax = fmaxf(tmax, fabsf(nv));
           if (GRAD) d->acc[off] = fmaf(d->fwd[(long long)P.fslot * d->fslot + off], delta, d->acc[off]);
         }
+      }
+      if (P.flags & kAbsMax) {
+        // the unit's maximum after injection (an injected node also counted
+        // its value before injection: an upper bound, which is all the
+        // snapshot scale needs)
+        float m = tmax;
+#pragma unroll
+        for (int k = 16; k > 0; k >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, k));
+        if (lane == 0 && m > 0.f) atomicMax(d->amax + P.amax_slot, __float_as_uint(m));
+        tmax = 0.f;
       }
       if (P.flags & kSample) {
         const int sbg = P.smp_ptr[u], se = P.smp_ptr[u + 1];

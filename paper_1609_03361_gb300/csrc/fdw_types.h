@@ -27,6 +27,7 @@ enum StepFlags : int {
   kInjectDiff = 8,   // inject (a - b) instead of a
   kTestStall = 16,   // test hook: the producer issues no loads, so every consumer
                      // wait runs out of its clock budget and reports an error
+  kAbsMax = 32,      // fold max |u^{n+1}| of every unit into amax[amax_slot] of its shot
 };
 
 // Per-shot description; lives in device memory, 128-byte aligned (tensor maps).
@@ -45,6 +46,7 @@ struct alignas(128) ShotDesc {
   const void* m;       // model as s = 1/m, pitched, type mtype
   const float* eta;    // eta*dt/2 profiles, [nx] then [ny] then [nz]
   const float* etaf;   // eta*dt/2 field, pitched (when kEtaField)
+  unsigned int* amax;  // per-snapshot absolute maxima (float bits), forward role
   int nx, ny, nz, nzp;
   int mtype;
   int smp_n;           // number of sampled points of the current role
@@ -96,6 +98,7 @@ struct StepParams {
   int stage_bytes;     // bytes of one pipeline stage
   int off_p, off_m, off_f, off_e;  // byte offsets inside a stage
   int off_a;           // byte offset of the gradient-accumulator tile (gradient)
+  int amax_slot;       // snapshot index of kAbsMax
   float dt2;           // dt^2
   float csum;          // sum of the centre weights over the axes
   float w[3][kMaxR + 1];  // dt^2 c_k / h_a^2, k = 0..r (k = 0 unused; see csum)

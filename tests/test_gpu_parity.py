@@ -158,12 +158,15 @@ def test_gradient_fp32_checkpoints(fw, k):
     assert rel_l2(g, ref) < TOL
 
 
-@pytest.mark.parametrize("stype,tol", [("f16", 1e-2), ("bf16", 5e-2)])
-def test_gradient_low_precision_snapshots(fw, stype, tol):
+# k = 1 takes the separate max pass of the snapshot scale; k >= 2 folds the
+# maximum into the two steps that produce each pair
+@pytest.mark.parametrize("stype,tol,k", [("f16", 1e-2, 10), ("bf16", 5e-2, 10), ("f16", 1e-2, 1),
+                                         ("f16", 1e-2, 2), ("bf16", 5e-2, 3)])
+def test_gradient_low_precision_snapshots(fw, stype, tol, k):
     pb = Problem((29, 26, 31), 10.0, 8, 6, 90, nsrc=1, nrec=8, seed=32)
     resid = pb.oracle_forward().astype(np.float32)
     s = pb.solver(fw)
-    s.forward_ckpt(pb.q32, 10, stype)
+    s.forward_ckpt(pb.q32, k, stype)
     g = s.gradient(resid)
     s.sync()
     s.close()
