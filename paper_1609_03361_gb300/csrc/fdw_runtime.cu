@@ -305,6 +305,9 @@ struct Plan {
   long long max_points = 0;
   long long max_slot = 0;            // floats per pitched field, largest shot
   int grad_stages = 0, grad_stages_tile = -1;  // pipeline depth of the gradient step
+  // one unit-ticket counter per step launch of a pass, zeroed at the pass start
+  int* d_tickets = nullptr;
+  int ticket_cap = 0, ticket_next = 0;
 
   void clear_graphs() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
@@ -320,6 +323,7 @@ struct Plan {
     release_lists();
     for (auto& d : d_desc) dfree(d);
     dfree(d_err);
+    dfree(d_tickets);
     dfree(d_pack);
     dfree(d_unpack);
     if (cap) cudaStreamDestroy(cap);
@@ -698,6 +702,15 @@ static void ensure_plan(Plan& pl) {
     pl.d_err = dalloc<int>(1);
     CK(cudaMemset(pl.d_err, 0, sizeof(int)));
   }
+  int nt_max = 1;
+  for (auto* c : pl.shots) nt_max = std::max(nt_max, c->nt);
+  const int cap = 2 * nt_max + 256;  // a gradient pass launches about 2 nt steps
+  if (pl.ticket_cap < cap) {
+    dfree(pl.d_tickets);
+    pl.d_tickets = dalloc<int>(cap);
+    CK(cudaMemset(pl.d_tickets, 0, sizeof(int) * cap));
+    pl.ticket_cap = cap;
+  }
   const std::vector<int> v = current_versions(pl);
   if (pl.built && v == pl.built_versions) return;
   if (!pl.built) choose_default_tiling(pl);
@@ -783,6 +796,12 @@ static const Plan::LaunchInfo& launch_info(Plan& pl, bool grad) {
   return pl.launch_cache.emplace(key, li).first->second;
 }
 
+// Zero the unit tickets of the launches that follow on stream s.
+static void reset_tickets(Plan& pl, cudaStream_t s) {
+  CK(cudaMemsetAsync(pl.d_tickets, 0, sizeof(int) * pl.ticket_cap, s));
+  pl.ticket_next = 0;
+}
+
 static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s) {
   const fdw_ctx* c0 = pl.shots[0];
   const bool etaf = plan_etaf(pl);
@@ -796,6 +815,8 @@ static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s) {
   P.shots = pl.d_desc[a.role];
   P.units = pl.d_units;
   P.nunits = nunits;
+  if (pl.ticket_next >= pl.ticket_cap) fail(FDW_ERR_ARG, "too many step launches in one pass");
+  P.ticket = pl.d_tickets + pl.ticket_next++;
   P.flags = a.flags | (etaf ? kEtaField : 0) | (pl.test_stall ? kTestStall : 0);
   P.inj_ptr = Ls.d_inj_ptr;
   P.inj_nodes = Ls.d_nodes;
@@ -872,6 +893,7 @@ static void run_graph(Plan& pl, const std::string& key, cudaStream_t s, F&& body
 // Forward time loop over all shots of a plan; snapshots every k steps if k > 0.
 static void forward_body(Plan& pl, int k, int stype, cudaStream_t s) {
   const int nt = pl.shots[0]->nt;
+  reset_tickets(pl, s);
   for (auto* c : pl.shots) CK(cudaMemsetAsync(c->u, 0, sizeof(float) * 2 * c->slot, s));
   int flags_base = 0;
   if (pl.max_src > 0) flags_base |= kInject;
@@ -908,6 +930,7 @@ static void forward_body(Plan& pl, int k, int stype, cudaStream_t s) {
 
 static void adjoint_body(Plan& pl, cudaStream_t s) {
   const int nt = pl.shots[0]->nt;
+  reset_tickets(pl, s);
   for (auto* c : pl.shots) CK(cudaMemsetAsync(c->lam, 0, sizeof(float) * 2 * c->slot, s));
   int flags = 0;
   if (pl.max_rec > 0) flags |= kInject;
@@ -922,6 +945,7 @@ static void adjoint_body(Plan& pl, cudaStream_t s) {
 
 static void gradient_body(Plan& pl, int k, int stype, bool diff, cudaStream_t s) {
   const int nt = pl.shots[0]->nt;
+  reset_tickets(pl, s);
   const size_t ns = pl.shots.size();
   for (auto* c : pl.shots) {
     CK(cudaMemsetAsync(c->lam, 0, sizeof(float) * 2 * c->slot, s));
@@ -1191,6 +1215,7 @@ static void tune_cache_store(const std::string& key, int t, int lx, int st) {
 
 static void plan_autotune(Plan& pl, int steps) {
   ensure_plan(pl);
+  steps = std::min(steps, pl.ticket_cap - 2);
   const std::string key = tune_key(pl);
   int bt = -1, blx = 0, bst = 0;
   if (!tune_cache_lookup(key, &bt, &blx, &bst)) {
@@ -1221,6 +1246,7 @@ static void plan_autotune(Plan& pl, int steps) {
             pl.hdesc[kRoleFwd][i] = make_desc(pl, pl.shots[i], kRoleFwd);
           upload_desc(pl, kRoleFwd, s);
           StepArgs a{kRoleFwd, 0, 1, 1, 0, 0, 0, 0, false};
+          reset_tickets(pl, s);
           for (int w = 0; w < 2; ++w) launch_step(pl, a, s);
           CK(cudaEventRecord(e0, s));
           for (int i = 0; i < steps; ++i) {

@@ -350,6 +350,10 @@ step_kernel(const __grid_constant__ StepParams P) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ int s_abort;
   __shared__ int s_issued;
+  // the unit that starts at each stage (index -1: no more units), written by
+  // the producer before the stage's first arrival, read by the consumers
+  __shared__ Unit s_unit[kMaxStages];
+  __shared__ int s_uidx[kMaxStages];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const int S = P.stages;
@@ -379,20 +383,33 @@ step_kernel(const __grid_constant__ StepParams P) {
       Cursor c{0, 0u};
       int issued = 0;
       const uint32_t bytes_u = YW * ZW * 4;
-      for (int u = blockIdx.x; u < P.nunits && !*abort_flag && !(P.flags & kTestStall);
-           u += gridDim.x) {
+      const bool stall = (P.flags & kTestStall) != 0;
+      auto grab = [&](int after) { return P.ticket ? atomicAdd(P.ticket, 1) : after + (int)gridDim.x; };
+      int u = stall ? P.nunits : (P.ticket ? atomicAdd(P.ticket, 1) : (int)blockIdx.x);
+      bool failed = false;
+      while (u < P.nunits && !failed) {
         const Unit un = P.units[u];
         const ShotDesc* d = P.shots + un.shot;
         const uint32_t bytes_in = TY * TZ * 4 + TY * TZ * (d->mtype == kF32 ? 4 : 2) +
                                   (GRAD ? 2 * TY * TZ * 4 : 0) +
                                   ((P.flags & kEtaField) ? TY * TZ * 4 : 0);
+        int next = P.nunits;
         for (int p = un.x0 - R; p < un.x1 + R; ++p) {
           const uint32_t full = full0 + 8 * c.stage, empty = empty0 + 8 * c.stage;
           if (issued >= S && !wait_or_abort(empty, c.phase ^ 1u, abort_flag)) {
             atomicOr(P.err, kErrTimeoutEmpty);
             *abort_flag = 1;
+            failed = true;
             break;
           }
+          if (p == un.x0 - R) {
+            s_unit[c.stage] = un;
+            s_uidx[c.stage] = u;
+          }
+          // the next unit is claimed while the last plane of this one is in
+          // flight: late enough to leave it to a CTA that is free earlier,
+          // early enough to hide the atomic behind the stages still queued
+          if (p == un.x1 + R - 1) next = grab(u);
           const bool inner = p >= un.x0 && p < un.x1;
           mbar_arrive_expect_tx(full, bytes_u + (inner ? bytes_in : 0u));
           const uint32_t sb = smem_u32(smem + c.stage * P.stage_bytes);
@@ -409,6 +426,18 @@ step_kernel(const __grid_constant__ StepParams P) {
           ++issued;
           c.next(S);
         }
+        u = next;
+      }
+      // end marker: a stage that carries no data and unit index -1
+      if (!failed && !stall) {
+        if (issued >= S && !wait_or_abort(empty0 + 8 * c.stage, c.phase ^ 1u, abort_flag)) {
+          atomicOr(P.err, kErrTimeoutEmpty);
+          *abort_flag = 1;
+        } else {
+          s_uidx[c.stage] = -1;
+          mbar_arrive(full0 + 8 * c.stage);
+          ++issued;
+        }
       }
       s_issued = issued;
     }
@@ -423,8 +452,15 @@ step_kernel(const __grid_constant__ StepParams P) {
     const int tid = threadIdx.x;
     float tmax = 0.f;  // max |u^{n+1}| of the thread's points in the current unit (kAbsMax)
     bool ok = true;
-    for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x) {
-      const Unit un = P.units[u];
+    while (true) {
+      // the stage of the next unit's first plane names the unit
+      if (!wait_or_abort(full0 + 8 * ca.stage, ca.phase, abort_flag)) {
+        ok = false;
+        break;
+      }
+      const int u = s_uidx[ca.stage];
+      if (u < 0) break;
+      const Unit un = s_unit[ca.stage];
       const ShotDesc* d = P.shots + un.shot;
       const int mtype = d->mtype;
       if (mtype == kF16)

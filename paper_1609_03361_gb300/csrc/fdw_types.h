@@ -16,6 +16,8 @@ namespace fdw {
 constexpr int kTZ = 32;
 // Largest stencil radius r = p/2 (space order 16).
 constexpr int kMaxR = 8;
+// Deepest pipeline of the step kernel.
+constexpr int kMaxStages = 2 * kMaxR + 8;
 
 enum MType : int { kF32 = 0, kF16 = 1, kBF16 = 2 };
 
@@ -82,6 +84,10 @@ struct StepParams {
   const ShotDesc* shots;
   const Unit* units;
   int nunits;
+  // Work distribution: with a ticket counter (zero before the launch) each CTA
+  // takes the next unit in table order when it is ready for one; without, CTA
+  // b takes units b, b + gridDim.x, ...
+  int* ticket;
   int flags;
   // injection: unit u owns nodes [inj_ptr[u], inj_ptr[u+1])
   const int* inj_ptr;
