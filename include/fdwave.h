@@ -244,6 +244,32 @@ fdw_status fdw_forward_static(int ndim, const int64_t* shape, const double* spac
                               const float* m, int nsrc, const double* src_xyz, const float* q,
                               int nrec, const double* rec_xyz, float* rec, void* stream);
 
+/* ---------------------------------------------------------- 2D diffusion */
+
+/* The diffusion example of Sec. 4: u_t = alpha (u_xx + u_yy) (Eq. 1), forward
+ * Euler in time and second-order 3-point differences per axis, on an
+ * [nx][ny] grid whose boundary rows and columns keep their initial values
+ * (only interior points are updated).  One step is
+ *   u'(i,j) = wc u(i,j) + wx (u(i-1,j) + u(i+1,j)) + wy (u(i,j-1) + u(i,j+1))
+ * with wx = dt alpha/dx^2, wy = dt alpha/dy^2, wc = 1 - 2wx - 2wy, in float32.
+ *   u       device float32 [nx][ny], y contiguous: the initial field on entry,
+ *           the field after `steps` steps once the stream reaches that point
+ *   tmp     device float32 [nx][ny] scratch, not overlapping u (its contents
+ *           on entry are ignored and undefined afterwards)
+ *   nx, ny  >= 3 (FDW_ERR_ARG), <= 2^31 (FDW_ERR_SHAPE)
+ *   dx, dy, alpha, dt  > 0 (FDW_ERR_ARG); dt above the Eq. 2 limit
+ *           dx^2 dy^2 / (2 alpha (dx^2 + dy^2)) gives FDW_ERR_CFL
+ *   steps   >= 0
+ *   steps_per_pass  time steps fused into one pass over memory: 1, 2, 4 or 8
+ *           (0 selects 4).  Results do not depend on it: every point sees the
+ *           same float32 operations in the same order.
+ *   stream  CUDA stream (NULL: the legacy default stream)
+ * The caller owns u and tmp.  Stream-ordered: the call returns once the work
+ * is enqueued; host or non-device pointers give FDW_ERR_ARG, a failed launch
+ * FDW_ERR_CUDA.  Allocates nothing. */
+fdw_status fdw_diffusion2d(float* u, float* tmp, int64_t nx, int64_t ny, double dx, double dy,
+                           double alpha, double dt, int steps, int steps_per_pass, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

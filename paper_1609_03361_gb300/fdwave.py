@@ -79,6 +79,7 @@ _SIGS = [
     ("fdw_batch_get_tiling", _I, [_P, ctypes.POINTER(_I)]),
     ("fdw_forward_static", _I, [_I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), _I, _I,
                                 _D, _I, _D, _P, _I, _P, _P, _I, _P, _P, _P]),
+    ("fdw_diffusion2d", _I, [_P, _P, ctypes.c_int64, ctypes.c_int64, _D, _D, _D, _D, _I, _I, _P]),
 ]
 
 
@@ -327,6 +328,25 @@ def fdw_forward_static(shape, spacing, space_order, nbl, dt, nt, vmax, m, src_xy
                                     _ptr(m, keep), src.shape[0], _ptr(src, keep, np.float64),
                                     _ptr(q, keep), rcv.shape[0], _ptr(rcv, keep, np.float64),
                                     _ptr(rec, keep), _stream(stream, device)))
+
+
+def fdw_diffusion2d(u, tmp, dx, dy, alpha, dt, steps, steps_per_pass=0, stream=None):
+    """2D diffusion of Sec. 4 in place on ``u`` (see include/fdwave.h): ``u`` and
+    ``tmp`` are contiguous float32 CUDA tensors of shape (nx, ny); ``tmp`` is
+    scratch (allocated here when None)."""
+    torch = _torch()
+    if not (_is_tensor(u) and u.is_cuda and u.dtype == torch.float32 and u.is_contiguous()
+            and u.dim() == 2):
+        raise FdwError(1, "u must be a contiguous 2-D float32 CUDA tensor (updated in place)")
+    if tmp is None:
+        tmp = torch.empty_like(u)
+    if tmp.shape != u.shape or tmp.dtype != u.dtype or not tmp.is_contiguous() or not tmp.is_cuda:
+        raise FdwError(1, "tmp must match u")
+    nx, ny = u.shape
+    _check(lib().fdw_diffusion2d(u.data_ptr(), tmp.data_ptr(), int(nx), int(ny), float(dx),
+                                 float(dy), float(alpha), float(dt), int(steps),
+                                 int(steps_per_pass), _stream(stream, u.device)))
+    return u
 
 
 # ------------------------------------------------------------------ objects

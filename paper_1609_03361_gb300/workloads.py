@@ -174,3 +174,18 @@ def fwi_shots(n=256, h=12.5, space_order=8, nt=2000, nbl=40, f_hz=15.0, nshots=1
                          base.velocity, np.array([[pos[i], pos[j], 40.0]]), base.rec)
             shots.append(w)
     return shots, anomaly(base.velocity)
+
+
+def diffusion_field(nx=1000, ny=1000, seed=0, noise=0.01):
+    """Initial field of the 2D diffusion example (Sec. 4): 1 on a centred square
+    of a quarter of each side, 0 elsewhere, plus seeded uniform noise of the
+    given amplitude (so that no symmetry hides an index error)."""
+    rng = np.random.default_rng(seed)
+    u = noise * (2.0 * rng.random((nx, ny)) - 1.0)
+    u[3 * nx // 8: 5 * nx // 8, 3 * ny // 8: 5 * ny // 8] += 1.0
+    return u
+
+
+def diffusion_dt(dx, dy, alpha=1.0):
+    """Largest stable forward-Euler step of Sec. 4, Eq. 2."""
+    return dx * dx * dy * dy / (2.0 * alpha * (dx * dx + dy * dy))

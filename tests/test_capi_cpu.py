@@ -86,3 +86,16 @@ def test_status_strings(fw):
     for st in range(10):
         assert L.fdw_status_string(st)
     assert L.fdw_version() >= 100
+
+
+def test_diffusion_host_checks(fw):
+    # argument checks that return before any device call (the pointers are
+    # never dereferenced)
+    f = fw.lib().fdw_diffusion2d
+    lim = 0.1 ** 4 / (2 * 1.0 * 2 * 0.1 ** 2)  # Eq. 2 for dx = dy = 0.1, alpha = 1
+    assert f(16, 32, 10, 10, 0.1, 0.1, 1.0, lim * 1.001, 3, 0, None) == 4   # FDW_ERR_CFL
+    assert f(16, 32, 10, 10, 0.1, 0.1, 1.0, lim, 3, 3, None) == 1         # steps_per_pass
+    assert f(16, 16, 10, 10, 0.1, 0.1, 1.0, lim, 3, 0, None) == 1         # u == tmp
+    assert f(16, 32, 2, 10, 0.1, 0.1, 1.0, lim, 3, 0, None) == 1          # nx < 3
+    assert f(16, 32, 10, 10, 0.1, 0.1, -1.0, lim, 3, 0, None) == 1        # alpha <= 0
+    assert f(None, 32, 10, 10, 0.1, 0.1, 1.0, lim, 3, 0, None) == 1       # null field
