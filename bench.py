@@ -234,7 +234,7 @@ def run_forward(args, world, rank, local):
         s.set_sources(w.src)
         s.set_receivers(w.rec)
     elif not args.no_autotune:
-        s.autotune(5)
+        s.autotune(20)
     tiling = s.tiling()
     stream = torch.cuda.current_stream(dev)
     for _ in range(args.warmup):
@@ -309,6 +309,7 @@ def run_forward(args, world, rank, local):
     if not args.no_extras:
         extras["batched"] = run_batched(args.batch_shots, 800, dev)
         extras["fwi"] = run_fwi(args.fwi_shots, args.fwi_nt, 10, dev)
+        extras["diffusion"] = run_diffusion(dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GPts/s", "n_gpus": world,
@@ -326,6 +327,65 @@ def run_forward(args, world, rank, local):
         line.update(extras)
         print(json.dumps(line), flush=True)
     s.close()
+
+
+def run_diffusion(dev):
+    """2D diffusion of Sec. 4: the 1000^2, 500-step example (L2-resident) and a
+    16384^2 grid (1 GiB per field, HBM-bound), GPts/s = point updates per
+    second from CUDA events; the example is checked against the FP64 oracle,
+    which is also timed on it (test infrastructure, as it stands)."""
+    import torch
+    import oracle
+    from paper_1609_03361_gb300 import fdwave as fw
+    from paper_1609_03361_gb300 import workloads as W
+    out = {"workload": "2D diffusion, forward Euler, 5-point, dt at the Eq. 2 limit"}
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(u0, dx, steps, spp, reps):
+        u = u0.clone()
+        tmp = torch.empty_like(u)
+        dt = W.diffusion_dt(dx, dx)
+        fw.fdw_diffusion2d(u, tmp, dx, dx, 1.0, dt, steps, spp)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        best = 1e30
+        for _ in range(reps):
+            u.copy_(u0)
+            e0.record(stream)
+            fw.fdw_diffusion2d(u, tmp, dx, dx, 1.0, dt, steps, spp)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            best = min(best, e0.elapsed_time(e1))
+        return u, best
+
+    u0h = W.diffusion_field(1000, 1000, seed=0).astype(np.float32)
+    u0 = torch.from_numpy(u0h).to(dev)
+    u, ms = timed(u0, 0.001, 500, 0, 5)
+    t = time.perf_counter()
+    ref = oracle.diffusion(u0h.astype(np.float64), 0.001, 0.001, 1.0, W.diffusion_dt(0.001, 0.001), 500)
+    el = time.perf_counter() - t
+    out["example_1000sq_500_steps"] = {
+        "gpts": 1e6 * 500 / (ms * 1e-3) / 1e9, "ms": ms, "steps_per_pass": 4,
+        "max_abs_err_vs_oracle": float(np.abs(u.cpu().numpy() - ref).max()),
+        "oracle_gpts": 1e6 * 500 / el / 1e9, "oracle_cores": 1}
+    del u, u0
+    big = torch.from_numpy(W.diffusion_field(4096, 4096, seed=1).astype(np.float32)).to(dev)
+    u0 = big.repeat(4, 4)   # 16384^2, 1 GiB per field
+    del big
+    peak, kind = measured_peaks()
+    res = {}
+    for spp in (1, 2, 4, 8):
+        _, ms = timed(u0, 1e-3, 32, spp, 3)
+        g = 16384 * 16384 * 32 / (ms * 1e-3) / 1e9
+        res[f"spp{spp}"] = {"gpts": g, "hbm_gbs_algorithmic": 8.0 * g / spp}
+    one = res["spp1"]["hbm_gbs_algorithmic"]
+    out["grid_16384sq_32_steps"] = res
+    out["roofline_1step"] = {"bound": "hbm", "bytes_per_point": 8, "achieved": one, "peak": peak,
+                             "unit": "GB/s", "frac": one / peak, "peak_kind": kind,
+                             "ceiling_gpts": peak / 8.0}
+    del u0
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batched(nshots, nt, dev, timed_reps=1):
@@ -350,7 +410,7 @@ def run_batched(nshots, nt, dev, timed_reps=1):
         recs.append(torch.empty((nt, w.rec.shape[0]), device=dev))
     updates = sum(int(np.prod(w.comp_shape)) for w in shots) * (nt - 1)
     b = fw.Batch(solvers)
-    b.autotune(3)
+    b.autotune(10)
     b.forward(qs, recs)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -587,7 +647,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--workload", default="forward", choices=["forward", "so16", "precision"])
+    ap.add_argument("--workload", default="forward",
+                    choices=["forward", "so16", "precision", "diffusion"])
     ap.add_argument("--nt", type=int, default=1000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -611,7 +672,10 @@ def main():
         dev = torch.device("cuda", local)
         torch.cuda.set_device(dev)
         if rank == 0:
-            (run_so16 if args.workload == "so16" else run_precision)(args, dev)
+            if args.workload == "diffusion":
+                print(json.dumps(run_diffusion(dev)), flush=True)
+            else:
+                (run_so16 if args.workload == "so16" else run_precision)(args, dev)
         return
     run_forward(args, world, rank, local)
     if world > 1:

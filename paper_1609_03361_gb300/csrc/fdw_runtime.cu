@@ -509,7 +509,9 @@ static void choose_default_tiling(Plan& pl) {
   bool all2d = true;
   for (auto* c : pl.shots)
     if (c->ny > 1) all2d = false;
-  pl.tile = pl.tile_req >= 0 ? pl.tile_req : (all2d ? 3 : 0);
+  // tile 4 (16 x 32 points, four consumer warps, 96 registers: four CTAs per
+  // SM) measured fastest or within noise of it on every 3D case tried
+  pl.tile = pl.tile_req >= 0 ? pl.tile_req : (all2d ? 3 : 4);
   const int ms = max_stages(pl, pl.tile);
   pl.stages = pl.stages_req > 0 ? std::min(pl.stages_req, ms) : std::min(pl.r + 4, ms);
   if (pl.stages < pl.r + 2) fail(FDW_ERR_ARG, "pipeline too shallow for this order");
@@ -1231,39 +1233,56 @@ static void plan_autotune(Plan& pl, int steps) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    float best = 1e30f;
+    // time `n` forward steps of one tiling (after two untimed ones), ms
+    auto time_config = [&](int t, int lx, int st, int n) {
+      pl.tile = t;
+      pl.lx = lx;
+      pl.stages = st;
+      build_lists(pl);
+      for (size_t i = 0; i < pl.shots.size(); ++i)
+        pl.hdesc[kRoleFwd][i] = make_desc(pl, pl.shots[i], kRoleFwd);
+      upload_desc(pl, kRoleFwd, s);
+      StepArgs a{kRoleFwd, 0, 1, 1, 0, 0, 0, 0, false};
+      reset_tickets(pl, s);
+      for (int w = 0; w < 2; ++w) launch_step(pl, a, s);
+      CK(cudaEventRecord(e0, s));
+      for (int i = 0; i < n; ++i) {
+        a.cur = i & 1; a.prev = a.out = (i + 1) & 1;
+        launch_step(pl, a, s);
+      }
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float ms_ = 0.f;
+      CK(cudaEventElapsedTime(&ms_, e0, e1));
+      return ms_;
+    };
+    // sweep every candidate once, then re-time the four fastest twice more,
+    // interleaved, and keep the best time of each: short timings of single
+    // configurations are noisy at the level that separates the leaders
+    std::vector<std::tuple<float, int, int, int>> cand;
     for (int t : tiles) {
       const int ms = max_stages(pl, t);
       for (int extra : {2, 3}) {
         const int st = std::min(pl.r + 1 + extra, ms);
         for (int lx : lxs) {
           if (lx > nxmax && lx != nxmax) continue;
-          pl.tile = t;
-          pl.lx = lx;
-          pl.stages = st;
-          build_lists(pl);
-          for (size_t i = 0; i < pl.shots.size(); ++i)
-            pl.hdesc[kRoleFwd][i] = make_desc(pl, pl.shots[i], kRoleFwd);
-          upload_desc(pl, kRoleFwd, s);
-          StepArgs a{kRoleFwd, 0, 1, 1, 0, 0, 0, 0, false};
-          reset_tickets(pl, s);
-          for (int w = 0; w < 2; ++w) launch_step(pl, a, s);
-          CK(cudaEventRecord(e0, s));
-          for (int i = 0; i < steps; ++i) {
-            a.cur = i & 1; a.prev = a.out = (i + 1) & 1;
-            launch_step(pl, a, s);
-          }
-          CK(cudaEventRecord(e1, s));
-          CK(cudaEventSynchronize(e1));
-          float ms_ = 0.f;
-          CK(cudaEventElapsedTime(&ms_, e0, e1));
-          if (ms_ < best) {
-            best = ms_;
-            bt = t; blx = lx; bst = st;
-          }
+          cand.emplace_back(time_config(t, lx, st, steps), t, lx, st);
         }
       }
     }
+    std::sort(cand.begin(), cand.end());
+    cand.resize(std::min<size_t>(cand.size(), 4));
+    const int n2 = std::min(2 * steps, pl.ticket_cap - 2);
+    for (int rep = 0; rep < 2; ++rep)
+      for (auto& c : cand) {
+        const float ms_ = time_config(std::get<1>(c), std::get<2>(c), std::get<3>(c), n2) *
+                          (float)steps / (float)n2;
+        std::get<0>(c) = std::min(std::get<0>(c), ms_);
+      }
+    std::sort(cand.begin(), cand.end());
+    bt = std::get<1>(cand[0]);
+    blx = std::get<2>(cand[0]);
+    bst = std::get<3>(cand[0]);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     plan_sync(pl);
