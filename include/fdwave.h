@@ -182,6 +182,36 @@ fdw_status fdw_sync(fdw_ctx* ctx);
  * cached there per (GPU, order, shape, model type).  Synchronises. */
 fdw_status fdw_autotune(fdw_ctx* ctx, int steps);
 
+/* Checkpoint memory budget of fdw_forward_ckpt / fdw_gradient: at most
+ * `max_pairs` checkpoint pairs (u^{n}, u^{n-1}) are stored (each the size of
+ * two fields in the snapshot type).  0 (the default) stores one pair per
+ * ckpt_every steps, (nt-1)/ckpt_every pairs, and the gradient recomputes each
+ * segment of ckpt_every steps once.  A smaller positive budget makes both
+ * calls follow a binomial checkpoint schedule over those segments (Griewank,
+ * "revolve"; the paper has no counterpart: it extends the checkpointed
+ * gradient of Sec. 5.4): the forward call stores the pairs that the schedule
+ * takes on its first sweep, and the gradient re-advances from stored pairs,
+ * storing and freeing pairs as it reverses, with the fewest forward steps any
+ * schedule with that many pairs can use (fdw_checkpoint_schedule gives the
+ * schedule).  With FP32 snapshots the gradient is bit for bit the one of the
+ * unlimited budget.  Takes effect at the next fdw_forward_ckpt (a gradient
+ * before it gives FDW_ERR_STATE).  Under a budget the gradient reuses the
+ * slots as it goes, so it consumes the checkpoints: each fdw_gradient needs
+ * its own fdw_forward_ckpt (FDW_ERR_STATE otherwise).  FDW_ERR_ARG if
+ * max_pairs < 0.  Host only. */
+fdw_status fdw_set_checkpoint_budget(fdw_ctx* ctx, int max_pairs);
+
+/* The binomial schedule used for nseg segments with nslots pairs, as (op, arg)
+ * pairs of ints: op 1 = advance the current state to the start of segment
+ * arg, 2 = store the current state in slot arg, 3 = make slot arg (-1: the
+ * zero state at time 0) the current state, 4 = recompute segment arg from the
+ * current state (its start) and run its adjoint steps.  The state at the
+ * start of segment 0 is current at the beginning.  Writes at most cap pairs
+ * into actions[2*cap] and returns the number of actions (larger than cap when
+ * actions was too short: nothing is written then), -1 for nseg < 1,
+ * nslots < 0, cap < 0 or actions NULL with cap > 0.  Host only. */
+int fdw_checkpoint_schedule(int nseg, int nslots, int* actions, int cap);
+
 /* Force a tile configuration: tile index (0..5, -1 = default; 3 is meant for
  * 2D grids), x-chunk length (0 = default) and pipeline depth (>= 2, 0 =
  * default). */

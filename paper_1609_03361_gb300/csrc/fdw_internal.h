@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "fdw_types.h"
 
 namespace fdw {
@@ -58,5 +60,17 @@ cudaError_t launch_grad_out(const float* acc, Geom g, float scale, float* out, i
                             int nbl, int ndim, int phys_x, int phys_y, int phys_z,
                             cudaStream_t s);
 cudaError_t launch_copy_out(const float* field, Geom g, float* out, cudaStream_t s);
+
+// Binomial checkpoint schedules over the segments of the gradient pass
+// (fdw_revolve.cu).
+enum CkptOp : int { kCkptAdvance = 1, kCkptTakeshot = 2, kCkptRestore = 3, kCkptReverse = 4 };
+struct CkptAction {
+  int op;
+  int arg;  // segment (advance, reverse) or slot (takeshot, restore; -1 = zero state)
+};
+// Fewest segment advances that reverse l segments from a held start state
+// with c free slots.
+long long revolve_cost(long long l, int c);
+std::vector<CkptAction> revolve_schedule(int nseg, int nslots);
 
 }  // namespace fdw

@@ -231,6 +231,8 @@ struct fdw_ctx {
 
   // checkpoint store
   int ckpt_k = 0, snap_type = -1, nsnap = 0;
+  int ckpt_budget = 0;          // most checkpoint pairs to store (0: one per k steps)
+  bool revolve = false;         // checkpoints follow a binomial schedule
   void* snaps = nullptr;
   unsigned int* amax = nullptr;
   float* seg = nullptr;         // k+1 slots
@@ -289,6 +291,12 @@ struct Plan {
   // aux descriptors for snapshots: [nsnap][nshots] pack and unpack
   AuxShot* d_pack = nullptr;
   AuxShot* d_unpack = nullptr;
+  // binomial schedule: actions, and snapshot descriptors [variant][slot][shot]
+  // (variant 0/1: the forward wavefield pair with u^{t} in slot 0/1, variant
+  // 2/3: the segment-buffer pair with the newer field in slot 0/1)
+  std::vector<CkptAction> rv_actions;
+  int rv_nseg = -1, rv_slots = -1;
+  AuxShot* d_rv = nullptr;
   int aux_version = -1;
   std::vector<int> built_versions;   // points/buffers versions the lists and maps were built for
   struct LaunchInfo {
@@ -326,6 +334,7 @@ struct Plan {
     dfree(d_tickets);
     dfree(d_pack);
     dfree(d_unpack);
+    dfree(d_rv);
     if (cap) cudaStreamDestroy(cap);
   }
 };
@@ -696,6 +705,18 @@ static std::vector<int> current_versions(const Plan& pl) {
   return v;
 }
 
+// At least `cap` unit-ticket counters; a larger array invalidates the graphs
+// that hold the old one.
+static void ensure_tickets(Plan& pl, long long cap) {
+  if (pl.ticket_cap >= cap) return;
+  if (cap > (1LL << 30)) fail(FDW_ERR_ARG, "too many step launches in one pass");
+  pl.clear_graphs();
+  dfree(pl.d_tickets);
+  pl.d_tickets = dalloc<int>((size_t)cap);
+  CK(cudaMemset(pl.d_tickets, 0, sizeof(int) * (size_t)cap));
+  pl.ticket_cap = (int)cap;
+}
+
 // (Re)build units, lists and descriptors when points, buffers or tiling changed.
 static void ensure_plan(Plan& pl) {
   set_device(pl.device);
@@ -706,13 +727,7 @@ static void ensure_plan(Plan& pl) {
   }
   int nt_max = 1;
   for (auto* c : pl.shots) nt_max = std::max(nt_max, c->nt);
-  const int cap = 2 * nt_max + 256;  // a gradient pass launches about 2 nt steps
-  if (pl.ticket_cap < cap) {
-    dfree(pl.d_tickets);
-    pl.d_tickets = dalloc<int>(cap);
-    CK(cudaMemset(pl.d_tickets, 0, sizeof(int) * cap));
-    pl.ticket_cap = cap;
-  }
+  ensure_tickets(pl, 2 * nt_max + 256);  // a gradient pass launches about 2 nt steps
   const std::vector<int> v = current_versions(pl);
   if (pl.built && v == pl.built_versions) return;
   if (!pl.built) choose_default_tiling(pl);
@@ -900,14 +915,32 @@ static void forward_body(Plan& pl, int k, int stype, cudaStream_t s) {
   int flags_base = 0;
   if (pl.max_src > 0) flags_base |= kInject;
   if (pl.max_rec > 0) flags_base |= kSample;
-  const int nsnap = k > 0 ? (nt - 1) / k : 0;
+  const bool rv = k > 0 && pl.shots[0]->revolve;
+  const int nsnap = k > 0 ? pl.shots[0]->nsnap : 0;
+  const size_t ns = pl.shots.size();
   if (nsnap > 0)
     for (auto* c : pl.shots) CK(cudaMemsetAsync(c->amax, 0, sizeof(unsigned) * nsnap, s));
   // 16-bit snapshots need max |u| of the pair: with k >= 2 the two steps that
   // produce u^{jk-1} and u^{jk} fold it into amax[j-1] as they go; k = 1 (each
-  // field in two pairs) takes a separate pass
+  // field in two pairs) and the binomial schedule take a separate pass
   const bool scaled = stype != kF32;
-  const bool fused_max = scaled && k >= 2;
+  const bool fused_max = scaled && k >= 2 && !rv;
+  // binomial schedule: this sweep stores the checkpoints that the schedule
+  // takes before its first reversal, and leaves the state at the start of
+  // the last segment in the segment buffer (slot 1: u^{a}, slot 0: u^{a-1})
+  std::map<int, int> take;  // segment -> slot
+  int last_start = -1;
+  if (rv) {
+    int cur = 0;
+    for (const CkptAction& act : pl.rv_actions) {
+      if (act.op == kCkptReverse) break;
+      if (act.op == kCkptAdvance) cur = act.arg;
+      else if (act.op == kCkptTakeshot) take[cur] = act.arg;
+    }
+    last_start = (pl.rv_nseg - 1) * k;
+    if (last_start == 0)
+      for (auto* c : pl.shots) CK(cudaMemsetAsync(c->seg, 0, sizeof(float) * 2 * c->slot, s));
+  }
   for (int n = 0; n + 1 < nt; ++n) {
     StepArgs a{kRoleFwd, n & 1, (n + 1) & 1, (n + 1) & 1, 0, n, n, flags_base, false};
     if (fused_max) {
@@ -918,9 +951,23 @@ static void forward_body(Plan& pl, int k, int stype, cudaStream_t s) {
       }
     }
     launch_step(pl, a, s);
-    if (k > 0 && (n + 1) % k == 0 && (n + 1) / k <= nsnap) {
+    const int t = n + 1;  // u^t was just made; it lives in wavefield slot t & 1
+    if (rv) {
+      auto it = t % k == 0 ? take.find(t / k) : take.end();
+      if (it != take.end()) {
+        const AuxShot* d = pl.d_rv + ((size_t)(t & 1) * nsnap + it->second) * ns;
+        if (scaled) CK(launch_absmax(d, (int)ns, pl.max_slot, s));
+        CK(launch_pack(d, (int)ns, pl.max_slot, stype, s));
+      }
+      if (t == last_start)
+        for (auto* c : pl.shots) {
+          CK(cudaMemcpyAsync(c->seg + c->slot, c->u + (size_t)(t & 1) * c->slot,
+                             sizeof(float) * c->slot, cudaMemcpyDeviceToDevice, s));
+          CK(cudaMemcpyAsync(c->seg, c->u + (size_t)((t - 1) & 1) * c->slot,
+                             sizeof(float) * c->slot, cudaMemcpyDeviceToDevice, s));
+        }
+    } else if (k > 0 && (n + 1) % k == 0 && (n + 1) / k <= nsnap) {
       const int j = (n + 1) / k;  // snapshot j holds (u^{jk}, u^{jk-1})
-      const size_t ns = pl.shots.size();
       if (scaled && !fused_max)
         CK(launch_absmax(pl.d_pack + (size_t)(j - 1) * ns, (int)ns, pl.max_slot, s));
       CK(launch_pack(pl.d_pack + (size_t)(j - 1) * ns, (int)ns, pl.max_slot, stype, s));
@@ -976,10 +1023,83 @@ static void gradient_body(Plan& pl, int k, int stype, bool diff, cudaStream_t s)
   }
 }
 
+// Gradient pass under the binomial schedule: executes the schedule from its
+// first reversal on.  The current forward state lives in segment-buffer slots
+// 0 and 1 (the newer field in slot p); advancing steps it in place.
+static void revolve_gradient_body(Plan& pl, int k, int stype, bool diff, cudaStream_t s) {
+  const int nt = pl.shots[0]->nt;
+  const size_t ns = pl.shots.size();
+  const int nsnap = pl.shots[0]->nsnap;
+  reset_tickets(pl, s);
+  for (auto* c : pl.shots) {
+    CK(cudaMemsetAsync(c->lam, 0, sizeof(float) * 2 * c->slot, s));
+    CK(cudaMemsetAsync(c->acc, 0, sizeof(float) * c->slot, s));
+  }
+  const int adj_flags = (pl.max_rec > 0 ? kInject : 0) | (diff ? kInjectDiff : 0);
+  const int rec_flags = pl.max_src > 0 ? kInject : 0;
+  int p = 1;                   // segment-buffer slot of the newer field of the current state
+  int cur = 0;                 // segment whose start state is current
+  std::vector<int> slot_seg(std::max(nsnap, 1), -1);  // segment held by each slot
+  bool started = false;
+  for (const CkptAction& act : pl.rv_actions) {
+    if (!started && act.op != kCkptReverse) {
+      // done by the forward sweep, which leaves the last segment's start current
+      if (act.op == kCkptAdvance) cur = act.arg;
+      else if (act.op == kCkptTakeshot) slot_seg[act.arg] = cur;
+      continue;
+    }
+    if (!started && cur != pl.rv_nseg - 1) fail(FDW_ERR_STATE, "checkpoint schedule out of step");
+    started = true;
+    if (act.op == kCkptAdvance) {
+      for (int n = cur * k; n < act.arg * k; ++n) {
+        StepArgs a{kRoleRec, p, 1 - p, 1 - p, 0, n, 0, rec_flags, false};
+        launch_step(pl, a, s);
+        p = 1 - p;
+      }
+      cur = act.arg;
+    } else if (act.op == kCkptTakeshot) {
+      const AuxShot* d = pl.d_rv + ((size_t)(2 + p) * nsnap + act.arg) * ns;
+      if (stype != kF32) {
+        for (auto* c : pl.shots) CK(cudaMemsetAsync(c->amax + act.arg, 0, sizeof(unsigned), s));
+        CK(launch_absmax(d, (int)ns, pl.max_slot, s));
+      }
+      CK(launch_pack(d, (int)ns, pl.max_slot, stype, s));
+      slot_seg[act.arg] = cur;
+    } else if (act.op == kCkptRestore) {
+      if (act.arg < 0) {
+        for (auto* c : pl.shots) CK(cudaMemsetAsync(c->seg, 0, sizeof(float) * 2 * c->slot, s));
+        cur = 0;
+      } else {
+        CK(launch_unpack(pl.d_rv + ((size_t)3 * nsnap + act.arg) * ns, (int)ns, pl.max_slot, stype, s));
+        cur = slot_seg[act.arg];
+      }
+      p = 1;
+    } else if (act.op == kCkptReverse) {
+      const int j = act.arg;
+      if (cur != j) fail(FDW_ERR_STATE, "checkpoint schedule out of step");
+      const int a0 = j * k, b0 = std::min((j + 1) * k, nt);
+      auto slot_of = [&](int t) { return t == a0 - 1 ? 1 - p : (t == a0 ? p : t - a0 + 1); };
+      for (int n = a0; n <= b0 - 2; ++n) {
+        StepArgs a{kRoleRec, slot_of(n), slot_of(n - 1), slot_of(n + 1), 0, n, 0, rec_flags, false};
+        launch_step(pl, a, s);
+      }
+      for (int kk = b0 - 1; kk >= std::max(a0, 1); --kk) {
+        StepArgs a{kRoleAdj, (kk + 1) & 1, kk & 1, kk & 1, slot_of(kk), kk, 0, adj_flags, true};
+        launch_step(pl, a, s);
+      }
+      cur = j;
+    }
+  }
+}
+
 // Checkpoint buffers of a context for k and snapshot type.
 static void ensure_ckpt(fdw_ctx* c, int k, int stype) {
-  const int nsnap = (c->nt - 1) / k;
-  if (c->ckpt_k != k || c->snap_type != stype || !c->seg) {
+  // pairs (u^{jk}, u^{jk-1}) for j = 1 .. (nt-1)/k cover every segment start;
+  // a smaller budget switches to the binomial schedule with that many slots
+  const int nfull = (c->nt - 1) / k;
+  const bool rv = c->ckpt_budget > 0 && c->ckpt_budget < nfull;
+  const int nsnap = rv ? c->ckpt_budget : nfull;
+  if (c->ckpt_k != k || c->snap_type != stype || !c->seg || c->revolve != rv || c->nsnap != nsnap) {
     dfree(c->snaps); dfree(c->amax); dfree(c->seg);
     c->snaps = nullptr; c->amax = nullptr; c->seg = nullptr;
     c->have_ckpt = false;
@@ -991,6 +1111,7 @@ static void ensure_ckpt(fdw_ctx* c, int k, int stype) {
     c->ckpt_k = k;
     c->snap_type = stype;
     c->nsnap = nsnap;
+    c->revolve = rv;
     c->buffers_version++;
   }
   if (!c->lam) {
@@ -1010,7 +1131,49 @@ static void ensure_aux(Plan& pl) {
   const int k = pl.shots[0]->ckpt_k;
   const int nsnap = pl.shots[0]->nsnap;
   const int ver = pl.shots[0]->buffers_version * 131 + k;
-  if (pl.aux_version == ver && pl.d_pack) return;
+  if (pl.aux_version == ver && (pl.d_pack || pl.d_rv)) return;
+  if (pl.shots[0]->revolve) {
+    const fdw_ctx* c0 = pl.shots[0];
+    const int nseg = (c0->nt + k - 1) / k;
+    pl.rv_actions = revolve_schedule(nseg, nsnap);
+    pl.rv_nseg = nseg;
+    pl.rv_slots = nsnap;
+    // step launches of the gradient pass: advances, recomputes and adjoint steps
+    long long launches = 0, cur = 0;
+    std::vector<long long> held(std::max(nsnap, 1), 0);
+    for (const CkptAction& a : pl.rv_actions) {
+      if (a.op == kCkptAdvance) {
+        launches += (long long)(a.arg - cur) * k;
+        cur = a.arg;
+      } else if (a.op == kCkptTakeshot) {
+        held[a.arg] = cur;
+      } else if (a.op == kCkptRestore) {
+        cur = a.arg < 0 ? 0 : held[a.arg];
+      } else {
+        launches += 2LL * k;
+      }
+    }
+    ensure_tickets(pl, launches + 256);
+    const size_t ns = pl.shots.size();
+    std::vector<AuxShot> d((size_t)4 * nsnap * ns);
+    for (int v = 0; v < 4; ++v)
+      for (int j = 0; j < nsnap; ++j)
+        for (size_t si = 0; si < ns; ++si) {
+          fdw_ctx* c = pl.shots[si];
+          AuxShot a;
+          a.n = c->slot;
+          a.snap = static_cast<unsigned char*>(c->snaps) + (size_t)c->slot * 2 * msize(c->snap_type) * j;
+          a.amax = c->amax + j;
+          float* base = v < 2 ? c->u : c->seg;
+          const int newer = v & 1;
+          a.a = base + (size_t)newer * c->slot;
+          a.b = base + (size_t)(1 - newer) * c->slot;
+          d[((size_t)v * nsnap + j) * ns + si] = a;
+        }
+    upload_vec((void**)&pl.d_rv, d.data(), d.size() * sizeof(AuxShot));
+    pl.aux_version = ver;
+    return;
+  }
   const size_t ns = pl.shots.size();
   std::vector<AuxShot> pack((size_t)std::max(nsnap, 1) * ns), unpack(pack.size());
   for (int j = 1; j <= nsnap; ++j)
@@ -1114,7 +1277,7 @@ static void plan_forward(Plan& pl, const float* const* q, float* const* rec, int
     upload_desc(pl, kRoleRec, s);
   }
   std::ostringstream key;
-  key << "fwd k" << k << " t" << stype;
+  key << "fwd k" << k << " t" << stype << " rv" << (k > 0 && pl.shots[0]->revolve ? pl.shots[0]->nsnap : 0);
   run_graph(pl, key.str(), s, [&](cudaStream_t st) { forward_body(pl, k, stype, st); });
   for (size_t i = 0; i < copies.size(); ++i)
     CK(cudaMemcpyAsync(copies[i].first, copies[i].second, sizes[i] * sizeof(float),
@@ -1152,9 +1315,17 @@ static void plan_gradient(Plan& pl, const float* const* resid, const float* cons
   upload_desc(pl, kRoleAdj, s);
   ensure_aux(pl);
   const int k = pl.shots[0]->ckpt_k, stype = pl.shots[0]->snap_type;
+  const bool rv = pl.shots[0]->revolve;
   std::ostringstream key;
-  key << "grad k" << k << " t" << stype << " d" << diff;
-  run_graph(pl, key.str(), s, [&](cudaStream_t st) { gradient_body(pl, k, stype, diff, st); });
+  key << "grad k" << k << " t" << stype << " d" << diff << " rv" << (rv ? pl.shots[0]->nsnap : 0);
+  run_graph(pl, key.str(), s, [&](cudaStream_t st) {
+    if (rv) revolve_gradient_body(pl, k, stype, diff, st);
+    else gradient_body(pl, k, stype, diff, st);
+  });
+  // the binomial schedule reuses the checkpoint slots and the current state
+  // as it reverses: a next gradient needs a new checkpointed forward
+  if (rv)
+    for (auto* c : pl.shots) c->have_ckpt = false;
   for (size_t i = 0; i < ns; ++i) {
     fdw_ctx* c = pl.shots[i];
     const size_t nout = layout == FDW_LAYOUT_COMPUTATIONAL ? (size_t)c->nx * c->ny * c->nz
@@ -1591,6 +1762,17 @@ fdw_status fdw_autotune(fdw_ctx* c, int steps) {
   });
 }
 
+fdw_status fdw_set_checkpoint_budget(fdw_ctx* c, int max_pairs) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    if (max_pairs < 0) fail(FDW_ERR_ARG, "checkpoint budget must be >= 0");
+    if (max_pairs != c->ckpt_budget) {
+      c->ckpt_budget = max_pairs;
+      c->have_ckpt = false;  // the stored checkpoints follow the old schedule
+    }
+  });
+}
+
 fdw_status fdw_set_tiling(fdw_ctx* c, int tile, int xchunk, int stages) {
   if (!c) return FDW_ERR_ARG;
   return guard(&c->err, [&] {
@@ -1663,6 +1845,9 @@ fdw_status fdw_batch_forward_ckpt(fdw_batch* b, const float* const* q, float* co
     if (k < 1) fail(FDW_ERR_ARG, "ckpt_every must be >= 1");
     if (stype != kF32 && stype != kF16 && stype != kBF16) fail(FDW_ERR_ARG, "bad snapshot type");
     check_compatible(b->shots);
+    for (auto* c : b->shots)
+      if (c->ckpt_budget != b->shots[0]->ckpt_budget)
+        fail(FDW_ERR_ARG, "shots of a batch need the same checkpoint budget");
     set_device(b->plan->device);
     for (auto* c : b->shots) ensure_ckpt(c, k, stype);
     ensure_plan(*b->plan);

@@ -80,6 +80,8 @@ _SIGS = [
     ("fdw_forward_static", _I, [_I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), _I, _I,
                                 _D, _I, _D, _P, _I, _P, _P, _I, _P, _P, _P]),
     ("fdw_diffusion2d", _I, [_P, _P, ctypes.c_int64, ctypes.c_int64, _D, _D, _D, _D, _I, _I, _P]),
+    ("fdw_set_checkpoint_budget", _I, [_P, _I]),
+    ("fdw_checkpoint_schedule", _I, [_I, _I, ctypes.POINTER(_I), _I]),
 ]
 
 
@@ -256,6 +258,23 @@ def fdw_autotune(ctx, steps=10):
 
 def fdw_set_tiling(ctx, tile=-1, xchunk=0, stages=0):
     _check(lib().fdw_set_tiling(ctx, int(tile), int(xchunk), int(stages)), ctx)
+
+
+def fdw_set_checkpoint_budget(ctx, max_pairs):
+    _check(lib().fdw_set_checkpoint_budget(ctx, int(max_pairs)), ctx)
+
+
+def fdw_checkpoint_schedule(nseg, nslots):
+    """Binomial checkpoint schedule as a list of (op, arg): 1 advance to
+    segment arg, 2 store in slot arg, 3 restore slot arg (-1: zero state),
+    4 reverse segment arg."""
+    n = lib().fdw_checkpoint_schedule(int(nseg), int(nslots), None, 0)
+    if n < 0:
+        raise FdwError(1, "bad schedule arguments")
+    buf = (ctypes.c_int * (2 * max(n, 1)))()
+    m = lib().fdw_checkpoint_schedule(int(nseg), int(nslots), buf, n)
+    assert m == n
+    return [(buf[2 * i], buf[2 * i + 1]) for i in range(n)]
 
 
 def fdw_get_tiling(ctx):
@@ -439,6 +458,9 @@ class Solver:
 
     def autotune(self, steps=10):
         fdw_autotune(self.ctx, steps)
+
+    def set_checkpoint_budget(self, max_pairs):
+        fdw_set_checkpoint_budget(self.ctx, max_pairs)
 
     def set_tiling(self, tile=-1, xchunk=0, stages=0):
         fdw_set_tiling(self.ctx, tile, xchunk, stages)
