@@ -535,8 +535,26 @@ def run_fwi(nshots, nt, k, dev, group=4):
         b.close()
     for sv in solvers:
         sv.close()
+    # the FP64 oracle's gradient (full forward history kept in host memory) on
+    # a bounded sample: the first shot over the first few time steps, scaled to
+    # nt steps (test infrastructure, timed as it stands)
+    import oracle
+    nts = 12
+    st = oracle.Setup(base.shape, base.spacing, base.space_order, base.nbl, dt, nts)
+    M = oracle.extend_model(st, base.m.astype(np.float32).astype(np.float64))
+    eta = oracle.damping(st, vmax)
+    q0 = shots[0].wavelet()[:nts, None].astype(np.float64)
+    r0 = np.random.default_rng(0).standard_normal((nts, nrec))
+    t0 = time.perf_counter()
+    oracle.forward(st, M, eta, shots[0].src, q0, base.rec)
+    oracle.gradient(st, M, eta, shots[0].src, q0, base.rec, r0)
+    t_oracle = (time.perf_counter() - t0) * (nt - 1) / (nts - 1)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"workload": f"{nshots} shots, 256^3 (336^3 computational), SO8, {nt} steps, "
                         f"checkpoints every {k} steps",
+            "oracle_s_per_shot": t_oracle,
+            "oracle_sample": f"first shot, {nts} time steps of forward + gradient on the full "
+                             f"grid, FP64, {cores} host cores, scaled to {nt} steps",
             "s_per_shot_plain_fp32": t_plain / nshots, "s_per_shot_batched_fp16": t_batch / nshots,
             "grad_rel_l2_batched_fp16_vs_plain_fp32": diff,
             "budget": {"pairs": budget, "checkpoint_gb": budget * pair_bytes / 1e9,
@@ -681,7 +699,7 @@ def main():
     ap.add_argument("--tiling", default="", help="tile,xchunk,stages instead of autotuning")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and FWI parts")
     ap.add_argument("--batch-shots", type=int, default=64)
-    ap.add_argument("--fwi-shots", type=int, default=4)
+    ap.add_argument("--fwi-shots", type=int, default=16)
     ap.add_argument("--fwi-nt", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mine":
