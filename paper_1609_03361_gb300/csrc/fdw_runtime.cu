@@ -301,7 +301,7 @@ struct Plan {
   std::vector<int> built_versions;   // points/buffers versions the lists and maps were built for
   struct LaunchInfo {
     const void* fn;
-    int grid, threads, stages;
+    int grid, threads, stages, cstages, cstage_bytes;
     size_t smem;
     int stage_bytes, off_p, off_m, off_f, off_a, off_e;
   };
@@ -449,18 +449,35 @@ static void compute_points(fdw_ctx* c, PointSet& ps, int n, const double* xyz) {
 
 // ---------------------------------------------------------------- plan
 
+// Shared-memory stages of a step launch.  The forward and adjoint steps stage
+// each plane's tiles with its halo plane; the gradient step, whose tiles are
+// twice the halo plane, keeps them in a second ring of stages that is only
+// occupied while they are in flight (the halo ring also holds the r planes of
+// the x stencil ahead of the plane being updated).
 struct StageLayout {
-  int off_p, off_m, off_f, off_a, off_e, bytes;
+  int off_p, off_m, off_f, off_a, off_e;  // tile offsets inside their stage
+  int bytes;    // halo-ring stage
+  int cbytes;   // second-ring stage (0: no second ring)
+  int r;
 };
 
 static int round128(int x) { return (x + 127) & ~127; }
 
+// Stages of the second ring for `stages` halo stages: the tiles of plane x
+// are issued with the halo plane x + r, so at most stages - r are in flight.
+static int second_ring_stages(const StageLayout& L, int stages) {
+  return L.cbytes ? std::max(2, stages - L.r) : 0;
+}
+
 static StageLayout stage_layout(int r, int tile, int mt_bytes, bool grad, bool etaf) {
+  const bool split = grad;  // a second ring measured slower for the forward step
   const int TY = tile_rows(kTiles[tile]);
   const int R4 = (r + 3) & ~3;
   const int ZW = kTZ + 2 * R4, YW = TY + 2 * r;
   StageLayout L;
-  int off = round128(YW * ZW * 4);
+  L.r = r;
+  const int halo = round128(YW * ZW * 4);
+  int off = split ? 0 : halo;
   L.off_p = off;
   off += round128(TY * kTZ * 4);
   L.off_m = off;
@@ -471,12 +488,15 @@ static StageLayout stage_layout(int r, int tile, int mt_bytes, bool grad, bool e
   if (grad) off += round128(TY * kTZ * 4);
   L.off_e = off;
   if (etaf) off += round128(TY * kTZ * 4);
-  L.bytes = off;
+  L.bytes = split ? halo : off;
+  L.cbytes = split ? off : 0;
   return L;
 }
 
 static size_t smem_bytes(const StageLayout& L, int stages) {
-  return (size_t)stages * L.bytes + (size_t)(2 * stages + 1) * 8 + 128;
+  const int sc = second_ring_stages(L, stages);
+  return (size_t)stages * L.bytes + (size_t)sc * L.cbytes + (size_t)(2 * stages + 2 * sc + 1) * 8 +
+         128;
 }
 
 static int plan_mtype(const Plan& pl) { return pl.shots[0]->mtype; }
@@ -496,7 +516,7 @@ static void configure_kernel(const void* fn, size_t smem) {
 
 // Occupancy-limited number of resident CTAs of a launch.
 static int resident_ctas(const Plan& pl, int tile, int stages, bool grad) {
-  const StageLayout L = stage_layout(pl.r, tile, 4, grad, true);
+  const StageLayout L = stage_layout(pl.r, tile, msize(plan_mtype(pl)), grad, plan_etaf(pl));
   const size_t smem = smem_bytes(L, stages);
   const void* fn = step_fn(pl.r, tile, grad);
   configure_kernel(fn, smem);
@@ -507,7 +527,7 @@ static int resident_ctas(const Plan& pl, int tile, int stages, bool grad) {
 }
 
 static int max_stages(const Plan& pl, int tile) {
-  const StageLayout L = stage_layout(pl.r, tile, 4, true, true);
+  const StageLayout L = stage_layout(pl.r, tile, 4, false, true);
   const int cap = device_smem_optin(pl.device) - 1024;  // static shared memory and slack
   int s = 2 * pl.r + 8;
   while (s > pl.r + 2 && (int)smem_bytes(L, s) > cap) --s;
@@ -528,7 +548,8 @@ static void choose_default_tiling(Plan& pl) {
     pl.lx = pl.lx_req;
     return;
   }
-  // aim at >= 4 units per resident CTA so the static schedule balances
+  // x chunks of 32 planes (the 2r warm-up planes of a chunk stay a minor
+  // share), halved while the grid gives fewer than two units per resident CTA
   const int slots = resident_ctas(pl, pl.tile, pl.stages, false);
   const int TY = tile_rows(kTiles[pl.tile]);
   long long cols = 0;
@@ -537,9 +558,9 @@ static void choose_default_tiling(Plan& pl) {
     cols += (long long)((c->ny + TY - 1) / TY) * ((c->nz + kTZ - 1) / kTZ);
     nxmax = std::max(nxmax, c->nx);
   }
-  long long chunks = (4LL * slots + cols - 1) / std::max(cols, 1LL);
-  chunks = std::max(1LL, std::min<long long>(chunks, nxmax));
-  pl.lx = std::max(8, (int)((nxmax + chunks - 1) / chunks));
+  int lx = std::min(32, nxmax);
+  while (lx > 8 && cols * ((nxmax + lx - 1) / lx) < 2LL * slots) lx /= 2;
+  pl.lx = std::max(1, lx);
 }
 
 static void upload_vec(void** dptr, const void* src, size_t bytes) {
@@ -798,6 +819,8 @@ static const Plan::LaunchInfo& launch_info(Plan& pl, bool grad) {
   Plan::LaunchInfo li;
   li.smem = smem_bytes(L, stages);
   li.stages = stages;
+  li.cstages = second_ring_stages(L, stages);
+  li.cstage_bytes = L.cbytes;
   li.fn = step_fn(pl.r, pl.tile, grad);
   configure_kernel(li.fn, li.smem);
   int nb = 0;
@@ -849,6 +872,8 @@ static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s) {
   P.amax_slot = a.amax_slot;
   P.stages = li.stages;
   P.stage_bytes = li.stage_bytes;
+  P.cstages = li.cstages;
+  P.cstage_bytes = li.cstage_bytes;
   P.off_p = li.off_p;
   P.off_m = li.off_m;
   P.off_f = li.off_f;

@@ -64,6 +64,16 @@ __device__ __forceinline__ void release_stage(uint32_t empty_bar, int lane) {
   if (lane == 0) mbar_arrive(empty_bar);
 }
 
+// The same for one stage of each ring.
+__device__ __forceinline__ void release_stages(uint32_t empty_a, uint32_t empty_b, int lane) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) {
+    mbar_arrive(empty_a);
+    mbar_arrive(empty_b);
+  }
+}
+
 __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort) {
   if (mbar_try_wait(bar, parity)) return true;
   long long t0 = clock64();
@@ -134,11 +144,14 @@ __device__ __forceinline__ void dbg_check(const char* what, float got, const flo
 // Streams one work unit through the pipeline: warm-up of the x queue, then
 // one update per plane of [x0, x1).  XU: the x loop is unrolled by the queue
 // length 2R+1 so that the queue slots rotate; otherwise the queue shifts by one
-// slot per plane (smaller code).  Returns false if a wait gave up.
-template <int R, int NY, int BY, bool GRAD, bool XU, typename MT>
+// slot per plane (smaller code).  SPLIT: the per-plane tiles come from the
+// second ring (cursor cc).  Returns false if a wait gave up.
+template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT, typename MT>
 __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, const ShotDesc* d,
                                          int u, const unsigned char* smem, uint32_t full0,
                                          uint32_t empty0, Cursor& ca, Cursor& cb,
+                                         const unsigned char* csmem, uint32_t cfull0,
+                                         uint32_t cempty0, Cursor& cc,
                                          volatile int* abort_flag, int lane, const Lanes L,
                                          float& tmax) {
   constexpr int TZ = kTZ;
@@ -232,9 +245,14 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
       // neighbours in y and z of plane x from the staged halo plane
       const unsigned char* sb = smem + cb.stage * P.stage_bytes;
       const float* U = reinterpret_cast<const float*>(sb);
+      const unsigned char* tb = sb;  // the plane's own tiles
+      if (SPLIT) {
+        if (!wait_or_abort(cfull0 + 8 * cc.stage, cc.phase, abort_flag)) return false;
+        tb = csmem + cc.stage * P.cstage_bytes;
+      }
       const float ex = ex_next;
       if (!etaf && x + 1 < un.x1) ex_next = eta_x[x + 1];
-      const float* Pp = reinterpret_cast<const float*>(sb + P.off_p);
+      const float* Pp = reinterpret_cast<const float*>(tb + P.off_p);
       const long long xoff = (long long)x * plane;
       // y neighbours of the thread's rows: local rows r0-R .. r0+NY-1+R
       float4 yr[NY + 2 * R];
@@ -269,9 +287,9 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
         }
         const int li = (r0 + j) * TZ + zl;
         const float4 pv = lds4(Pp + li);
-        const float4 sv = load_quad<MT>(sb + P.off_m, li);
+        const float4 sv = load_quad<MT>(tb + P.off_m, li);
         float4 ev;
-        if (etaf) ev = lds4(reinterpret_cast<const float*>(sb + P.off_e) + li);
+        if (etaf) ev = lds4(reinterpret_cast<const float*>(tb + P.off_e) + li);
         else ev = make_float4(ex + eyz[j][0], ex + eyz[j][1], ex + eyz[j][2], ex + eyz[j][3]);
 #pragma unroll
         for (int v = 0; v < kVZ; ++v) {
@@ -292,13 +310,18 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
           if (GRAD) d2t[j][v] = val[j][v] - 2.f * c + prev;  // second time difference of lambda
         }
         if (GRAD) {
-          fw[j] = lds4(reinterpret_cast<const float*>(sb + P.off_f) + li);
-          aw[j] = lds4(reinterpret_cast<const float*>(sb + P.off_a) + li);
+          fw[j] = lds4(reinterpret_cast<const float*>(tb + P.off_f) + li);
+          aw[j] = lds4(reinterpret_cast<const float*>(tb + P.off_a) + li);
         }
       }
       // every read of the staged planes is done: hand them back before the
       // global stores, which only read registers
-      release_stage(empty0 + 8 * cb.stage, lane);
+      if (SPLIT) {
+        release_stages(empty0 + 8 * cb.stage, cempty0 + 8 * cc.stage, lane);
+        cc.next(P.cstages);
+      } else {
+        release_stage(empty0 + 8 * cb.stage, lane);
+      }
       if (x + R >= un.x1) release_stage(empty0 + 8 * ahead_stage, lane);
       cb.next(S);
       if (amx) {  // points past the grid compute to zero and do not move the maximum
@@ -337,7 +360,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
   return true;
 }
 
-template <int R, int NY, int BY, bool GRAD, bool XU>
+template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT = GRAD>
 __global__ void __launch_bounds__((BY + 1) * 32)
 step_kernel(const __grid_constant__ StepParams P) {
   constexpr int TZ = kTZ;
@@ -357,11 +380,16 @@ step_kernel(const __grid_constant__ StepParams P) {
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const int S = P.stages;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * P.stage_bytes);
+  const int SC = SPLIT ? P.cstages : 0;
+  const unsigned char* csmem = smem + S * P.stage_bytes;  // second ring (SPLIT)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S * P.stage_bytes + SC * P.cstage_bytes);
   const uint32_t full0 = smem_u32(bars);
   const uint32_t empty0 = smem_u32(bars + S);
-  const uint32_t tail = smem_u32(bars + 2 * S);  // consumer-only barrier at the end of a unit
+  const uint32_t cfull0 = smem_u32(bars + 2 * S);
+  const uint32_t cempty0 = smem_u32(bars + 2 * S + SC);
+  const uint32_t tail = smem_u32(bars + 2 * S + 2 * SC);  // consumer-only barrier at the end of a unit
   volatile int* abort_flag = &s_abort;
+  __shared__ int s_issued_c;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -370,9 +398,14 @@ step_kernel(const __grid_constant__ StepParams P) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, BY);
     }
+    for (int s = 0; s < SC; ++s) {
+      mbar_init(cfull0 + 8 * s, 1);
+      mbar_init(cempty0 + 8 * s, BY);
+    }
     mbar_init(tail, NCONS);
     s_abort = 0;
     s_issued = 0;
+    s_issued_c = 0;
     fence_barrier_init();
   }
   __syncthreads();
@@ -381,7 +414,8 @@ step_kernel(const __grid_constant__ StepParams P) {
     // ------------------------------ producer ------------------------------
     if (lane == 0) {
       Cursor c{0, 0u};
-      int issued = 0;
+      Cursor c2{0, 0u};  // second ring (SPLIT)
+      int issued = 0, issued_c = 0;
       const uint32_t bytes_u = YW * ZW * 4;
       const bool stall = (P.flags & kTestStall) != 0;
       auto grab = [&](int after) { return P.ticket ? atomicAdd(P.ticket, 1) : after + (int)gridDim.x; };
@@ -410,21 +444,40 @@ step_kernel(const __grid_constant__ StepParams P) {
           // flight: late enough to leave it to a CTA that is free earlier,
           // early enough to hide the atomic behind the stages still queued
           if (p == un.x1 + R - 1) next = grab(u);
-          const bool inner = p >= un.x0 && p < un.x1;
-          mbar_arrive_expect_tx(full, bytes_u + (inner ? bytes_in : 0u));
+          // the per-plane tiles of plane q: with the halo plane q itself, or
+          // (SPLIT) in the second ring together with the halo plane q + R
+          const int q = SPLIT ? p - R : p;
+          const bool inner = q >= un.x0 && q < un.x1;
+          mbar_arrive_expect_tx(full, bytes_u + (!SPLIT && inner ? bytes_in : 0u));
           const uint32_t sb = smem_u32(smem + c.stage * P.stage_bytes);
           tma_load_4d(sb, &d->tm_uh, un.z0 - R4, un.y0 - R, p, P.cur, full);
-          if (inner) {
-            tma_load_4d(sb + P.off_p, &d->tm_uc, un.z0, un.y0, p, P.prev, full);
-            tma_load_3d(sb + P.off_m, &d->tm_m, un.z0, un.y0, p, full);
-            if (GRAD) {
-              tma_load_4d(sb + P.off_f, &d->tm_f, un.z0, un.y0, p, P.fslot, full);
-              tma_load_3d(sb + P.off_a, &d->tm_a, un.z0, un.y0, p, full);
-            }
-            if (P.flags & kEtaField) tma_load_3d(sb + P.off_e, &d->tm_e, un.z0, un.y0, p, full);
-          }
           ++issued;
           c.next(S);
+          if (inner) {
+            uint32_t tb = sb, tfull = full;
+            if (SPLIT) {
+              tfull = cfull0 + 8 * c2.stage;
+              if (issued_c >= SC && !wait_or_abort(cempty0 + 8 * c2.stage, c2.phase ^ 1u, abort_flag)) {
+                atomicOr(P.err, kErrTimeoutEmpty);
+                *abort_flag = 1;
+                failed = true;
+                break;
+              }
+              mbar_arrive_expect_tx(tfull, bytes_in);
+              tb = smem_u32(csmem + c2.stage * P.cstage_bytes);
+            }
+            tma_load_4d(tb + P.off_p, &d->tm_uc, un.z0, un.y0, q, P.prev, tfull);
+            tma_load_3d(tb + P.off_m, &d->tm_m, un.z0, un.y0, q, tfull);
+            if (GRAD) {
+              tma_load_4d(tb + P.off_f, &d->tm_f, un.z0, un.y0, q, P.fslot, tfull);
+              tma_load_3d(tb + P.off_a, &d->tm_a, un.z0, un.y0, q, tfull);
+            }
+            if (P.flags & kEtaField) tma_load_3d(tb + P.off_e, &d->tm_e, un.z0, un.y0, q, tfull);
+            if (SPLIT) {
+              ++issued_c;
+              c2.next(SC);
+            }
+          }
         }
         u = next;
       }
@@ -440,6 +493,7 @@ step_kernel(const __grid_constant__ StepParams P) {
         }
       }
       s_issued = issued;
+      s_issued_c = issued_c;
     }
   } else {
     // ------------------------------ consumers -----------------------------
@@ -448,6 +502,7 @@ step_kernel(const __grid_constant__ StepParams P) {
     L.zl = kVZ * (lane & 7);
     Cursor ca{0, 0u};   // read-ahead cursor: every plane in order (centre values)
     Cursor cb{0, 0u};   // compute cursor: the plane being updated
+    Cursor cc{0, 0u};   // second-ring cursor (SPLIT): the plane being updated
     uint32_t tail_phase = 0u;
     const int tid = threadIdx.x;
     float tmax = 0.f;  // max |u^{n+1}| of the thread's points in the current unit (kAbsMax)
@@ -464,13 +519,13 @@ step_kernel(const __grid_constant__ StepParams P) {
       const ShotDesc* d = P.shots + un.shot;
       const int mtype = d->mtype;
       if (mtype == kF16)
-        ok = run_unit<R, NY, BY, GRAD, XU, __half>(P, un, d, u, smem, full0, empty0, ca, cb,
+        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, __half>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
                                                abort_flag, lane, L, tmax);
       else if (mtype == kBF16)
-        ok = run_unit<R, NY, BY, GRAD, XU, __nv_bfloat16>(P, un, d, u, smem, full0, empty0, ca, cb,
+        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, __nv_bfloat16>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
                                                       abort_flag, lane, L, tmax);
       else
-        ok = run_unit<R, NY, BY, GRAD, XU, float>(P, un, d, u, smem, full0, empty0, ca, cb,
+        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, float>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
                                               abort_flag, lane, L, tmax);
       if (!ok) break;
 
@@ -553,6 +608,14 @@ step_kernel(const __grid_constant__ StepParams P) {
       const uint32_t ph = (uint32_t)((k / S) & 1);
       long long t0 = clock64();
       while (!mbar_try_wait(full0 + 8 * st, ph) && clock64() - t0 < kWaitBudget) {
+      }
+    }
+    const int issued_c = s_issued_c;
+    for (int k = (issued_c > SC ? issued_c - SC : 0); k < issued_c; ++k) {
+      const int st = k % SC;
+      const uint32_t ph = (uint32_t)((k / SC) & 1);
+      long long t0 = clock64();
+      while (!mbar_try_wait(cfull0 + 8 * st, ph) && clock64() - t0 < kWaitBudget) {
       }
     }
   }

@@ -100,9 +100,16 @@ struct StepParams {
   int smp_row;         // time row of the recorded samples
   int cur, prev, out;  // wavefield slots: u^n, u^{n-1}, u^{n+1} (out may equal prev)
   int fslot;           // forward-wavefield slot (gradient)
-  int stages;          // pipeline depth
+  int stages;          // pipeline depth (halo planes of u^n)
   int stage_bytes;     // bytes of one pipeline stage
-  int off_p, off_m, off_f, off_e;  // byte offsets inside a stage
+  // Gradient steps keep the per-plane tiles (u^{n-1}, model, forward field,
+  // accumulator, damping) in a ring of their own, loaded with the halo plane
+  // R planes ahead and freed as soon as the plane is updated: cstages stages
+  // of cstage_bytes, the offsets below relative to a stage of that ring.
+  // Otherwise cstages = 0 and the tiles share the halo plane's stage.
+  int cstages;
+  int cstage_bytes;
+  int off_p, off_m, off_f, off_e;  // byte offsets of the per-plane tiles
   int off_a;           // byte offset of the gradient-accumulator tile (gradient)
   int amax_slot;       // snapshot index of kAbsMax
   float dt2;           // dt^2
