@@ -1429,21 +1429,49 @@ static void plan_autotune(Plan& pl, int steps) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    // the timed steps inject (zeros) and sample like a real forward step, into
+    // scratch wavelet and trace rows of their own
+    const int rows = 2 * steps + 2;
+    struct Scratch {  // freed on every exit
+      std::vector<float*> v;
+      float* add(size_t n) {
+        v.push_back(nullptr);
+        v.back() = dalloc<float>(n);
+        return v.back();
+      }
+      ~Scratch() {
+        for (float* p : v) dfree(p);
+      }
+    } scratch;
+    std::vector<float*> tq, trec;
+    for (auto* c : pl.shots) {
+      tq.push_back(scratch.add((size_t)rows * std::max(1, c->src.n)));
+      CK(cudaMemsetAsync(tq.back(), 0, sizeof(float) * rows * std::max(1, c->src.n), s));
+      trec.push_back(scratch.add((size_t)rows * std::max(1, c->rec.n)));
+    }
+    int flags = 0;
+    if (pl.max_src > 0) flags |= kInject;
+    if (pl.max_rec > 0) flags |= kSample;
     // time `n` forward steps of one tiling (after two untimed ones), ms
     auto time_config = [&](int t, int lx, int st, int n) {
       pl.tile = t;
       pl.lx = lx;
       pl.stages = st;
       build_lists(pl);
-      for (size_t i = 0; i < pl.shots.size(); ++i)
+      for (size_t i = 0; i < pl.shots.size(); ++i) {
         pl.hdesc[kRoleFwd][i] = make_desc(pl, pl.shots[i], kRoleFwd);
+        pl.hdesc[kRoleFwd][i].inj_a = tq[i];
+        pl.hdesc[kRoleFwd][i].inj_b = nullptr;
+        pl.hdesc[kRoleFwd][i].smp_out = trec[i];
+      }
       upload_desc(pl, kRoleFwd, s);
-      StepArgs a{kRoleFwd, 0, 1, 1, 0, 0, 0, 0, false};
+      StepArgs a{kRoleFwd, 0, 1, 1, 0, 0, 0, flags, false};
       reset_tickets(pl, s);
       for (int w = 0; w < 2; ++w) launch_step(pl, a, s);
       CK(cudaEventRecord(e0, s));
       for (int i = 0; i < n; ++i) {
         a.cur = i & 1; a.prev = a.out = (i + 1) & 1;
+        a.inj_row = a.smp_row = i + 2;
         launch_step(pl, a, s);
       }
       CK(cudaEventRecord(e1, s));
@@ -1469,7 +1497,7 @@ static void plan_autotune(Plan& pl, int steps) {
     std::sort(cand.begin(), cand.end());
     cand.resize(std::min<size_t>(cand.size(), 4));
     const int n2 = std::min(2 * steps, pl.ticket_cap - 2);
-    for (int rep = 0; rep < 2; ++rep)
+    for (int rep = 0; rep < 3; ++rep)
       for (auto& c : cand) {
         const float ms_ = time_config(std::get<1>(c), std::get<2>(c), std::get<3>(c), n2) *
                           (float)steps / (float)n2;
