@@ -575,30 +575,62 @@ static void build_lists(Plan& pl) {
   pl.clear_graphs();
   const int TY = tile_rows(kTiles[pl.tile]);
   pl.units.clear();
-  std::vector<int> shot_first(pl.shots.size() + 1, 0);
-  std::vector<std::array<int, 3>> counts(pl.shots.size());
+  // Rows of units: an x range of one shot times all its (y, z) column tiles,
+  // in x order, shot after shot.  CTAs take units in this order, so the last
+  // round of units is cut short: rows from the end of the table are split
+  // into quarters (at least 8 planes) until one resident CTA's worth of units
+  // is small, which shortens the idle tail when the tickets run out.
+  struct Row {
+    int shot, x0, x1, base;
+    bool split;
+  };
+  std::vector<Row> rows;
+  std::vector<std::array<int, 2>> cols(pl.shots.size());
   for (size_t s = 0; s < pl.shots.size(); ++s) {
     const fdw_ctx* c = pl.shots[s];
-    const int cx = (c->nx + pl.lx - 1) / pl.lx, cy = (c->ny + TY - 1) / TY, cz = (c->nz + kTZ - 1) / kTZ;
-    counts[s] = {cx, cy, cz};
-    shot_first[s] = (int)pl.units.size();
-    for (int i = 0; i < cx; ++i)
-      for (int j = 0; j < cy; ++j)
-        for (int k = 0; k < cz; ++k) {
-          Unit u{};
-          u.shot = (int)s;
-          u.x0 = i * pl.lx;
-          u.x1 = std::min(c->nx, (i + 1) * pl.lx);
-          u.y0 = j * TY;
-          u.z0 = k * kTZ;
-          pl.units.push_back(u);
-        }
+    cols[s] = {(c->ny + TY - 1) / TY, (c->nz + kTZ - 1) / kTZ};
+    for (int x0 = 0; x0 < c->nx; x0 += pl.lx)
+      rows.push_back(Row{(int)s, x0, std::min(c->nx, x0 + pl.lx), 0, false});
   }
-  shot_first[pl.shots.size()] = (int)pl.units.size();
+  {
+    const long long tail = resident_ctas(pl, pl.tile, pl.stages, false);
+    long long covered = 0;
+    for (size_t i = rows.size(); i-- > 0 && covered < tail;) {
+      covered += (long long)cols[rows[i].shot][0] * cols[rows[i].shot][1];
+      rows[i].split = true;
+    }
+  }
+  std::vector<Row> fine;
+  for (const Row& r : rows) {
+    const int len = r.x1 - r.x0;
+    const int piece = std::max(8, (len + 3) / 4);
+    if (!r.split || len <= piece) {
+      fine.push_back(r);
+      continue;
+    }
+    for (int x0 = r.x0; x0 < r.x1; x0 += piece)
+      fine.push_back(Row{r.shot, x0, std::min(r.x1, x0 + piece), 0, true});
+  }
+  std::vector<std::vector<int>> xrow(pl.shots.size());
+  for (size_t s = 0; s < pl.shots.size(); ++s) xrow[s].assign(pl.shots[s]->nx, -1);
+  for (size_t ri = 0; ri < fine.size(); ++ri) {
+    Row& r = fine[ri];
+    r.base = (int)pl.units.size();
+    for (int x = r.x0; x < r.x1; ++x) xrow[r.shot][x] = (int)ri;
+    for (int j = 0; j < cols[r.shot][0]; ++j)
+      for (int k = 0; k < cols[r.shot][1]; ++k) {
+        Unit u{};
+        u.shot = r.shot;
+        u.x0 = r.x0;
+        u.x1 = r.x1;
+        u.y0 = j * TY;
+        u.z0 = k * kTZ;
+        pl.units.push_back(u);
+      }
+  }
   const int U = (int)pl.units.size();
   auto unit_of = [&](int s, int x, int y, int z) {
-    const auto& n = counts[s];
-    return shot_first[s] + ((x / pl.lx) * n[1] + y / TY) * n[2] + z / kTZ;
+    return fine[xrow[s][x]].base + (y / TY) * cols[s][1] + z / kTZ;
   };
   pl.max_rec = pl.max_src = 0;
   pl.max_points = 0;
