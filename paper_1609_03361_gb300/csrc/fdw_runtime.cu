@@ -1456,7 +1456,7 @@ static void plan_autotune(Plan& pl, int steps) {
       nxmax = std::max(nxmax, c->nx);
     }
     std::vector<int> tiles = all2d ? std::vector<int>{3} : std::vector<int>{0, 1, 2, 4, 5};
-    std::vector<int> lxs = {16, 32, 64, 128, nxmax};
+    std::vector<int> lxs = {16, 32, 48, 64, 80, 96, 128, nxmax};
     cudaStream_t s = pl.cap;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
