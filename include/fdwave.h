@@ -177,7 +177,9 @@ fdw_status fdw_sync(fdw_ctx* ctx);
 
 /* Brute-force search over tile shapes, x-chunk lengths and pipeline depths
  * (Sec. 3.3.3: block sizes found by a brute-force search), timing `steps`
- * forward steps each on the current model.  The choice is kept by the
+ * forward steps each on the current model (injecting zeros and sampling into
+ * scratch rows, as a real step does), then timing the four fastest again,
+ * interleaved and longer, and keeping the best.  The choice is kept by the
  * context and, when the environment variable FDW_AUTOTUNE_CACHE names a file,
  * cached there per (GPU, order, shape, model type).  Synchronises. */
 fdw_status fdw_autotune(fdw_ctx* ctx, int steps);
@@ -213,8 +215,9 @@ fdw_status fdw_set_checkpoint_budget(fdw_ctx* ctx, int max_pairs);
 int fdw_checkpoint_schedule(int nseg, int nslots, int* actions, int cap);
 
 /* Force a tile configuration: tile index (0..5, -1 = default; 3 is meant for
- * 2D grids), x-chunk length (0 = default) and pipeline depth (>= 2, 0 =
- * default). */
+ * 2D grids), x-chunk length (0 = default) and pipeline depth of the forward
+ * and adjoint steps (>= r + 2 with r = space_order / 2, 0 = default; the
+ * gradient step picks its own).  FDW_ERR_ARG outside these ranges. */
 fdw_status fdw_set_tiling(fdw_ctx* ctx, int tile, int xchunk, int stages);
 
 /* Tile configuration in use: out[0] = tile index, out[1] = x-chunk length,
