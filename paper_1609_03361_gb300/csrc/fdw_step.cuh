@@ -610,12 +610,14 @@ step_kernel(const __grid_constant__ StepParams P) {
       while (!mbar_try_wait(full0 + 8 * st, ph) && clock64() - t0 < kWaitBudget) {
       }
     }
-    const int issued_c = s_issued_c;
-    for (int k = (issued_c > SC ? issued_c - SC : 0); k < issued_c; ++k) {
-      const int st = k % SC;
-      const uint32_t ph = (uint32_t)((k / SC) & 1);
-      long long t0 = clock64();
-      while (!mbar_try_wait(cfull0 + 8 * st, ph) && clock64() - t0 < kWaitBudget) {
+    if constexpr (SPLIT) {
+      const int issued_c = s_issued_c;
+      for (int k = (issued_c > SC ? issued_c - SC : 0); k < issued_c; ++k) {
+        const int st = k % SC;
+        const uint32_t ph = (uint32_t)((k / SC) & 1);
+        long long t0 = clock64();
+        while (!mbar_try_wait(cfull0 + 8 * st, ph) && clock64() - t0 < kWaitBudget) {
+        }
       }
     }
   }
