@@ -59,6 +59,33 @@ def test_taylor_second_order(fw):
     assert all(3.0 < x < 5.0 for x in ratios), (ratios, errs)
 
 
+def test_taylor_64cubed_400_steps(fw):
+    """The reduced FWI case: 64^3 physical grid, SO8, 400 steps, FP16
+    snapshots every 10 steps, data from a +5 % Gaussian velocity anomaly."""
+    pb = Problem((64, 64, 64), 12.5, 8, 10, 400, nsrc=1, nrec=64, seed=17, f_hz=15.0)
+    g3 = np.stack(np.meshgrid(*[np.arange(64) - 31.5] * 3, indexing="ij"))
+    v_true = pb.v * (1 + 0.05 * np.exp(-(g3 ** 2).sum(0) / (2 * 8.0 ** 2)))
+    s = pb.solver(fw)
+    s.set_model((1 / v_true ** 2).astype(np.float32))
+    d = s.forward(pb.q32).astype(np.float64)
+    m0 = pb.m32.astype(np.float64)
+    J0, r = _J(s, m0, pb.q32, d)
+    s.set_model(pb.m32)
+    s.forward_ckpt(pb.q32, 10, "f16")
+    g = s.gradient(r.astype(np.float32), None, "physical").astype(np.float64)
+    dm = (1 / v_true ** 2 - m0)          # towards the true model
+    gd = float(np.sum(g * dm))
+    errs = []
+    for k in range(4):
+        h = 0.5 / 2 ** k
+        Jh, _ = _J(s, m0 + h * dm, pb.q32, d)
+        errs.append(abs(Jh - J0 - h * gd))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    s.close()
+    assert gd < 0                        # the true model lowers the misfit
+    assert all(3.0 < x < 5.0 for x in ratios), (ratios, errs)
+
+
 def test_gradient_matches_central_differences(fw):
     pb, s, d = _setup(fw)
     m0 = pb.m32.astype(np.float64)
