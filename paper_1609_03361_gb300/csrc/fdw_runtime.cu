@@ -613,24 +613,53 @@ static void build_lists(Plan& pl) {
   }
   std::vector<std::vector<int>> xrow(pl.shots.size());
   for (size_t s = 0; s < pl.shots.size(); ++s) xrow[s].assign(pl.shots[s]->nx, -1);
+  for (size_t ri = 0; ri < fine.size(); ++ri)
+    for (int x = fine[ri].x0; x < fine[ri].x1; ++x) xrow[fine[ri].shot][x] = (int)ri;
+  // Within a row, units that carry sparse work at their tail (receiver and
+  // source nodes: sampling in the forward step, injection of the residual in
+  // the adjoint step) come first, so that the last units of a row, and of
+  // the launch, are the light ones.
+  std::vector<std::vector<int>> weight(fine.size());
+  for (size_t ri = 0; ri < fine.size(); ++ri)
+    weight[ri].assign((size_t)cols[fine[ri].shot][0] * cols[fine[ri].shot][1], 0);
+  for (size_t si = 0; si < pl.shots.size(); ++si) {
+    const fdw_ctx* c = pl.shots[si];
+    for (const PointSet* ps : {&c->rec, &c->src})
+      for (int j = 0; j < ps->n; ++j)
+        for (int cc = 0; cc < 8; ++cc) {
+          if (ps->w[(size_t)j * 8 + cc] == 0.f) continue;
+          const int x = ps->base[(size_t)j * 3] + ((cc >> 2) & 1);
+          const int y = ps->base[(size_t)j * 3 + 1] + ((cc >> 1) & 1);
+          const int z = ps->base[(size_t)j * 3 + 2] + (cc & 1);
+          weight[xrow[si][x]][(size_t)(y / TY) * cols[si][1] + z / kTZ]++;
+        }
+  }
+  std::vector<std::vector<int>> pos(fine.size());  // local tile index -> place in its row
   for (size_t ri = 0; ri < fine.size(); ++ri) {
     Row& r = fine[ri];
     r.base = (int)pl.units.size();
-    for (int x = r.x0; x < r.x1; ++x) xrow[r.shot][x] = (int)ri;
-    for (int j = 0; j < cols[r.shot][0]; ++j)
-      for (int k = 0; k < cols[r.shot][1]; ++k) {
-        Unit u{};
-        u.shot = r.shot;
-        u.x0 = r.x0;
-        u.x1 = r.x1;
-        u.y0 = j * TY;
-        u.z0 = k * kTZ;
-        pl.units.push_back(u);
-      }
+    const int ck = cols[r.shot][1];
+    const std::vector<int>& w = weight[ri];
+    std::vector<int> order(w.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
+    pos[ri].assign(order.size(), 0);
+    for (size_t q = 0; q < order.size(); ++q) {
+      const int li = order[q];
+      pos[ri][li] = (int)q;
+      Unit u{};
+      u.shot = r.shot;
+      u.x0 = r.x0;
+      u.x1 = r.x1;
+      u.y0 = (li / ck) * TY;
+      u.z0 = (li % ck) * kTZ;
+      pl.units.push_back(u);
+    }
   }
   const int U = (int)pl.units.size();
   auto unit_of = [&](int s, int x, int y, int z) {
-    return fine[xrow[s][x]].base + (y / TY) * cols[s][1] + z / kTZ;
+    const int ri = xrow[s][x];
+    return fine[ri].base + pos[ri][(y / TY) * cols[s][1] + z / kTZ];
   };
   pl.max_rec = pl.max_src = 0;
   pl.max_points = 0;
