@@ -129,3 +129,34 @@ def test_autograd_function_matches_oracle(fw):
             np.add.at(fold[cx, cy], cz, ref[x, y])
     s.close()
     assert rel_l2(g, fold) < 1e-4
+
+
+def test_fwi_gradient_full_grid_first_steps(fw):
+    """The FWI workload's gradient on its full 336^3 computational grid (SO8,
+    the first FWI shot) over a short window of 14 steps, against the FP64
+    oracle's exact discrete gradient (which keeps the whole forward history:
+    about 4 GB here), with FP32 checkpoints every 10 steps in the default
+    tiling the bench's FWI uses."""
+    import oracle
+    from paper_1609_03361_gb300 import workloads as W
+    nt = 14
+    shots, _ = W.fwi_shots(nt=nt, nshots=16)
+    w = shots[0]
+    w.dt = W.choose_dt(oracle.dt_max(3, w.spacing, w.space_order, w.vmax))
+    dev = torch.device("cuda", 0)
+    s = fw.Solver(w.shape, w.spacing, w.space_order, w.nbl, w.dt, nt, w.vmax)
+    s.set_model(torch.from_numpy(w.m.astype(np.float32)).to(dev))
+    s.set_sources(w.src)
+    s.set_receivers(w.rec)
+    q = torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev)
+    resid = np.random.default_rng(21).standard_normal((nt, w.rec.shape[0])).astype(np.float32)
+    s.forward_ckpt(q, 10, "f32")
+    g = s.gradient(torch.from_numpy(resid).to(dev)).cpu().numpy()
+    s.sync()
+    s.close()
+    st = oracle.Setup(w.shape, w.spacing, w.space_order, w.nbl, w.dt, nt)
+    M = oracle.extend_model(st, w.m.astype(np.float32).astype(np.float64))
+    ref = oracle.gradient(st, M, oracle.damping(st, w.vmax), w.src,
+                          q.cpu().numpy().astype(np.float64), w.rec, resid.astype(np.float64))
+    assert np.abs(ref).max() > 0
+    assert rel_l2(g, ref) < 1e-4

@@ -285,30 +285,43 @@ def test_config_2d_101_so4_500_steps(fw):
     assert rel_l2(rec, ref) < TOL
 
 
-def test_config_3d_256_so8_full_grid_first_steps(fw):
-    """The 256^3 SO8 workload on its full 336^3 computational grid and in the
-    tiling the benchmark uses, compared with the oracle over its first 24
-    steps (the oracle needs ~1 s per step on this grid)."""
+@pytest.fixture(scope="module")
+def full_grid_case():
+    """The 256^3 SO8 workload on its full 336^3 computational grid over its
+    first 24 steps, with the oracle's traces and last field (the oracle needs
+    about 1 s per step on this grid)."""
     import oracle
     from paper_1609_03361_gb300 import workloads as W
     nt = 24
     w = W.config_3d(256, 12.5, 8, nt)
     w.dt = W.choose_dt(oracle.dt_max(3, w.spacing, w.space_order, w.vmax))
+    q = w.wavelet().astype(np.float32)[:, None]
+    st = oracle.Setup(w.shape, w.spacing, w.space_order, w.nbl, w.dt, nt)
+    M = oracle.extend_model(st, w.m.astype(np.float32).astype(np.float64))
+    ref, uref = oracle.forward(st, M, oracle.damping(st, w.vmax), w.src, q.astype(np.float64),
+                               w.rec, final=True)
+    return w, q, ref, uref
+
+
+# the autotuner's choice (as in the bench) and the tilings the bench's tuner
+# has picked on the GB300 (tile 4 with x chunks of 80 and 64, 7 stages)
+@pytest.mark.parametrize("tiling", [None, (4, 80, 7), (4, 64, 7)])
+def test_config_3d_256_so8_full_grid_first_steps(fw, full_grid_case, tiling):
+    w, q32, ref, uref = full_grid_case
     dev = torch.device("cuda", 0)
     s = fw.Solver(w.shape, w.spacing, w.space_order, w.nbl, w.dt, w.nt, w.vmax)
+    if tiling is not None:
+        s.set_tiling(*tiling)
     s.set_model(torch.from_numpy(w.m.astype(np.float32)).to(dev))
     s.set_sources(w.src)
     s.set_receivers(w.rec)
-    q = torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev)
-    s.autotune(2)
+    q = torch.from_numpy(q32).to(dev)
+    if tiling is None:
+        s.autotune(2)
     rec = s.forward(q).cpu().numpy()
     u = s.wavefield(0, like=q).cpu().numpy()
     s.sync()
     s.close()
-    st = oracle.Setup(w.shape, w.spacing, w.space_order, w.nbl, w.dt, nt)
-    M = oracle.extend_model(st, w.m.astype(np.float32).astype(np.float64))
-    ref, uref = oracle.forward(st, M, oracle.damping(st, w.vmax), w.src,
-                               q.cpu().numpy().astype(np.float64), w.rec, final=True)
     assert np.abs(ref).max() > 0
     assert rel_l2(rec, ref) < TOL
     assert rel_l2(u, uref) < TOL
