@@ -325,3 +325,43 @@ def test_config_3d_256_so8_full_grid_first_steps(fw, full_grid_case, tiling):
     assert np.abs(ref).max() > 0
     assert rel_l2(rec, ref) < TOL
     assert rel_l2(u, uref) < TOL
+
+
+def test_batched_config_full_grids_first_steps(fw):
+    """The 64-shot batched workload (cubes of 96^3..192^3 physical plus the
+    layer, SO8) launched as one batch over its first 16 steps; the smallest
+    and the largest shot are compared with the FP64 oracle on their full
+    grids, and every shot's traces must be finite."""
+    import oracle
+    from paper_1609_03361_gb300 import workloads as W
+    nt = 16
+    shots = W.batched_shots(nshots=64, nt=nt)
+    vmax = max(w.vmax for w in shots)
+    dt = W.choose_dt(oracle.dt_max(3, shots[0].spacing, 8, vmax))
+    dev = torch.device("cuda", 0)
+    solvers, qs = [], []
+    for w in shots:
+        w.dt = dt
+        s = fw.Solver(w.shape, w.spacing, 8, w.nbl, dt, nt, vmax)
+        s.set_model(torch.from_numpy(w.m.astype(np.float32)).to(dev))
+        s.set_sources(w.src)
+        s.set_receivers(w.rec)
+        solvers.append(s)
+        qs.append(torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev))
+    b = fw.Batch(solvers)
+    recs = [r.cpu().numpy() for r in b.forward(qs)]
+    for s in solvers:
+        s.sync()
+    b.close()
+    for s in solvers:
+        s.close()
+    assert all(np.isfinite(r).all() for r in recs)
+    sides = [w.shape[0] for w in shots]
+    for i in {int(np.argmin(sides)), int(np.argmax(sides))}:
+        w = shots[i]
+        st = oracle.Setup(w.shape, w.spacing, 8, w.nbl, dt, nt)
+        M = oracle.extend_model(st, w.m.astype(np.float32).astype(np.float64))
+        ref = oracle.forward(st, M, oracle.damping(st, vmax), w.src,
+                             qs[i].cpu().numpy().astype(np.float64), w.rec)
+        assert np.abs(ref).max() > 0
+        assert rel_l2(recs[i], ref) < TOL
