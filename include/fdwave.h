@@ -249,6 +249,61 @@ fdw_status fdw_batch_gradient(fdw_batch* b, const float* const* resid,
 fdw_status fdw_batch_autotune(fdw_batch* b, int steps);
 fdw_status fdw_batch_get_tiling(fdw_batch* b, int* out5);
 
+/* ------------------------------------------------ single-shot domain split */
+
+/* One x slab of a grid too large for one GPU (Sec. 6 names MPI parallelism
+ * only between whole inversion operators; splitting one grid across devices
+ * is an extension the paper does not have): the context holds the
+ * computational x planes [x_begin, x_end) of the grid that fdw_create would
+ * build from the same arguments, plus r = space_order/2 ghost planes on either
+ * side, and updates only its own planes.  x_end - x_begin >= r.  The model
+ * (fdw_set_model, either layout) and damping field (fdw_set_damping) are given
+ * for the whole grid, and source and receiver coordinates for the whole
+ * domain: the slab injects the source corners in its planes and records the
+ * receivers whose base plane (the lower x corner) it owns, leaving zeros in the
+ * other receivers' columns, so that summing the slabs' traces gives the traces
+ * of the whole grid.  Whole time loops (fdw_forward, fdw_forward_ckpt,
+ * fdw_adjoint, fdw_gradient, batches) give FDW_ERR_STATE / FDW_ERR_ARG on a
+ * slab: it advances with fdw_step, and after each step the caller copies
+ * each neighbour's send planes into this slab's ghost planes
+ * (fdw_halo_planes).  FDW_ERR_SHAPE for a range outside the grid. */
+fdw_status fdw_create_slab(fdw_ctx** out, int ndim, const int64_t* shape, const double* spacing,
+                           int space_order, int nbl, double dt, int nt, double vmax, int device,
+                           int64_t x_begin, int64_t x_end);
+
+/* One forward time step n (0 <= n <= nt-2) of any context: u^{n+1} from u^n
+ * and u^{n-1} (Sec. 5, Eq. 3 and Listing 6), injection of q^n, and the
+ * receiver samples rec^n of u^n; n = nt-1 records rec^{nt-1} only (for a slab,
+ * after the last ghost exchange).  n = 0 first clears the wavefields.  Calls
+ * n = 0 .. nt-1 in order compute what fdw_forward computes.  q [nt][nsrc] and
+ * rec [nt][nrec] are device arrays (FDW_ERR_ARG otherwise); stream-ordered. */
+fdw_status fdw_step(fdw_ctx* ctx, int n, const float* q, float* rec, void* stream);
+
+/* Device addresses, in the field u^{n+1} that fdw_step(n) produced, of a
+ * slab's first r and last r own planes (send_lo, send_hi) and of its lower and
+ * upper ghost planes (recv_lo, recv_hi), each a contiguous block of *count
+ * floats (r planes of ny x nzp; nzp = nz rounded up to a multiple of 32 in 3D,
+ * the same layout in every slab of a grid).  Before step n+1 the caller copies
+ * the lower neighbour's send_hi into recv_lo and the upper neighbour's send_lo
+ * into recv_hi (the outermost slabs keep zero ghosts: the zero halo of the
+ * scheme).  FDW_ERR_ARG for a context that is not a slab.  Host only. */
+fdw_status fdw_halo_planes(fdw_ctx* ctx, int n, float** send_lo, float** send_hi,
+                           float** recv_lo, float** recv_hi, int64_t* count);
+
+/* The exchange after step n between two neighbouring slabs of one grid held
+ * by this process (lower: the one with the smaller x planes), possibly on
+ * different devices: lower's send_hi to upper's recv_lo and upper's send_lo to
+ * lower's recv_hi, enqueued on `stream`.  FDW_ERR_ARG for slabs that are not
+ * neighbours of one grid. */
+fdw_status fdw_exchange_ghosts(fdw_ctx* lower, fdw_ctx* upper, int n, void* stream);
+
+/* Copies between a slab's ghost-plane blocks after step n and caller buffers
+ * of *count floats each (fdw_halo_planes), host or device, for exchanges
+ * through a communication library: dir 0 copies the send planes out (send_lo
+ * to lo, send_hi to hi), dir 1 copies lo into recv_lo and hi into recv_hi.  A
+ * NULL buffer skips its side.  Stream-ordered. */
+fdw_status fdw_halo_copy(fdw_ctx* ctx, int n, int dir, float* lo, float* hi, void* stream);
+
 /* ---------------------------------------------------------- allocation-free */
 
 /* Forward modelling that allocates nothing.  The paper has no counterpart:

@@ -56,14 +56,18 @@ __global__ void sample_kernel(const ShotDesc* shots, int slot, int row) {
   }
 }
 
+// The field may be an x slab of a larger grid: local plane x is plane x + xoff
+// of the full computational grid of nxg planes (xoff = 0, nxg = g.nx for a
+// whole grid); planes beyond the full grid take the nearest edge plane.
 __global__ void model_kernel(const float* in, int layout, int px, int py, int pz, int nbl,
-                             int ndim, void* out, int mtype, Geom g) {
+                             int ndim, void* out, int mtype, Geom g, int xoff, int nxg) {
   const long long n = dense_points(g);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const long long z = i % g.nz;
     const long long y = (i / g.nz) % g.ny;
-    const long long x = i / ((long long)g.nz * g.ny);
+    long long x = i / ((long long)g.nz * g.ny) + xoff;
+    x = x < 0 ? 0 : (x > nxg - 1 ? nxg - 1 : x);
     float v;
     if (layout == 0) {  // physical: clamp each computational index into the physical range
       long long cx = x - nbl, cy = (ndim == 3) ? y - nbl : 0, cz = z - nbl;
@@ -72,7 +76,7 @@ __global__ void model_kernel(const float* in, int layout, int px, int py, int pz
       cz = cz < 0 ? 0 : (cz > pz - 1 ? pz - 1 : cz);
       v = in[(cx * py + cy) * pz + cz];
     } else {
-      v = in[i];
+      v = in[(x * g.ny + y) * g.nz + z];
     }
     const long long o = pitched(g, i);
     const float sv = 1.0f / v;  // stored as s = 1/m (squared velocity)
@@ -82,11 +86,16 @@ __global__ void model_kernel(const float* in, int layout, int px, int py, int pz
   }
 }
 
-__global__ void eta_field_kernel(const float* in, float scale, float* out, Geom g) {
+__global__ void eta_field_kernel(const float* in, float scale, float* out, Geom g, int xoff,
+                                 int nxg) {
   const long long n = dense_points(g);
+  const long long pl = (long long)g.ny * g.nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    out[pitched(g, i)] = in[i] * scale;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long x = i / pl + xoff;
+    x = x < 0 ? 0 : (x > nxg - 1 ? nxg - 1 : x);
+    out[pitched(g, i)] = in[x * pl + i % pl] * scale;
+  }
 }
 
 // Snapshot kernels work on whole pitched fields, four floats per access: the
@@ -258,14 +267,16 @@ cudaError_t launch_sample(const ShotDesc* shots, int nshots, int maxpts, int slo
 }
 
 cudaError_t launch_model(const float* in, int layout, int px, int py, int pz, int nbl, int ndim,
-                         void* out, int mtype, Geom g, cudaStream_t s) {
-  model_kernel<<<blocks_for(dense_points(g)), kThreads, 0, s>>>(in, layout, px, py, pz, nbl, ndim,
-                                                                out, mtype, g);
+                         void* out, int mtype, Geom g, cudaStream_t s, int xoff, int nxg) {
+  model_kernel<<<blocks_for(dense_points(g)), kThreads, 0, s>>>(
+      in, layout, px, py, pz, nbl, ndim, out, mtype, g, xoff, nxg > 0 ? nxg : g.nx);
   return cudaGetLastError();
 }
 
-cudaError_t launch_eta_field(const float* in, float scale, float* out, Geom g, cudaStream_t s) {
-  eta_field_kernel<<<blocks_for(dense_points(g)), kThreads, 0, s>>>(in, scale, out, g);
+cudaError_t launch_eta_field(const float* in, float scale, float* out, Geom g, cudaStream_t s,
+                             int xoff, int nxg) {
+  eta_field_kernel<<<blocks_for(dense_points(g)), kThreads, 0, s>>>(in, scale, out, g, xoff,
+                                                                    nxg > 0 ? nxg : g.nx);
   return cudaGetLastError();
 }
 

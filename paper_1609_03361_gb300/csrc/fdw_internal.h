@@ -47,9 +47,13 @@ struct AuxShot {
 
 cudaError_t launch_sample(const ShotDesc* shots, int nshots, int maxpts, int slot, int row,
                           cudaStream_t s);
+// xoff, nxg: the field is an x slab, local plane x = plane x + xoff of a full
+// computational grid of nxg planes (nxg = 0: the field is the whole grid)
 cudaError_t launch_model(const float* in, int layout, int phys_x, int phys_y, int phys_z,
-                         int nbl, int ndim, void* out, int mtype, Geom g, cudaStream_t s);
-cudaError_t launch_eta_field(const float* in, float scale, float* out, Geom g, cudaStream_t s);
+                         int nbl, int ndim, void* out, int mtype, Geom g, cudaStream_t s,
+                         int xoff = 0, int nxg = 0);
+cudaError_t launch_eta_field(const float* in, float scale, float* out, Geom g, cudaStream_t s,
+                             int xoff = 0, int nxg = 0);
 // maxn: the largest field (floats per pitched slot) of the shots
 cudaError_t launch_absmax(const AuxShot* shots, int nshots, long long maxn, cudaStream_t s);
 cudaError_t launch_pack(const AuxShot* shots, int nshots, long long maxn, int stype,

@@ -232,6 +232,11 @@ struct fdw_ctx {
   // checkpoint store
   int ckpt_k = 0, snap_type = -1, nsnap = 0;
   int ckpt_budget = 0;          // most checkpoint pairs to store (0: one per k steps)
+  // x slab of a larger grid (fdw_create_slab): local plane i is plane i + gx0
+  // of the full computational grid of nx_full planes; the planes
+  // [own0, own1) are updated here, the r planes on either side are ghosts
+  bool slab = false;
+  int gx0 = 0, nx_full = 0, own0 = 0, own1 = 0;
   bool revolve = false;         // checkpoints follow a binomial schedule
   void* snaps = nullptr;
   unsigned int* amax = nullptr;
@@ -399,7 +404,9 @@ static void set_device(int dev) { CK(cudaSetDevice(dev)); }
 
 // ---------------------------------------------------------------- points
 
-static void compute_points(fdw_ctx* c, PointSet& ps, int n, const double* xyz) {
+// samples: the set is sampled (receivers of the forward step) rather than
+// injected; it decides which points a slab keeps.
+static void compute_points(fdw_ctx* c, PointSet& ps, int n, const double* xyz, bool samples) {
   if (n < 0 || (n > 0 && !xyz)) fail(FDW_ERR_ARG, "bad point array");
   PointSet out;
   out.n = n;
@@ -427,13 +434,31 @@ static void compute_points(fdw_ctx* c, PointSet& ps, int n, const double* xyz) {
       b[a] = (int)i + c->nbl;
       f[a] = xi - (double)i;
     }
+    // a slab keeps local x indices: a source keeps the corners in its planes,
+    // a receiver is kept whole by the slab that owns its base plane (its
+    // other corners are read from the ghost planes); everything else gets zero
+    // weights and a base inside the slab, so it is never touched
+    bool keep_point = true;
+    if (c->slab) {
+      b[0] -= c->gx0;
+      if (samples && (b[0] < c->own0 || b[0] >= c->own1)) {
+        keep_point = false;
+        b[0] = c->own0;
+      }
+    }
     for (int a = 0; a < 3; ++a) out.base[(size_t)j * 3 + a] = (c->ndim == 2 && a == 1) ? 0 : b[a];
     for (int cc = 0; cc < 8; ++cc) {
       const int bx = (cc >> 2) & 1, by = (cc >> 1) & 1, bz = cc & 1;
       double w = (bx ? f[0] : 1.0 - f[0]) * (bz ? f[2] : 1.0 - f[2]);
       if (c->ndim == 3) w *= by ? f[1] : 1.0 - f[1];
       else if (by) w = 0.0;
+      if (!keep_point) w = 0.0;
+      if (c->slab && !samples && (b[0] + bx < c->own0 || b[0] + bx >= c->own1)) w = 0.0;
       out.w[(size_t)j * 8 + cc] = (float)w;
+    }
+    if (c->slab && !samples) {  // a base outside the slab: keep it inside (weights are zero)
+      const int bxl = out.base[(size_t)j * 3];
+      if (bxl + 1 < c->own0 || bxl >= c->own1) out.base[(size_t)j * 3] = c->own0;
     }
   }
   if (n > 0) {
@@ -589,8 +614,8 @@ static void build_lists(Plan& pl) {
   for (size_t s = 0; s < pl.shots.size(); ++s) {
     const fdw_ctx* c = pl.shots[s];
     cols[s] = {(c->ny + TY - 1) / TY, (c->nz + kTZ - 1) / kTZ};
-    for (int x0 = 0; x0 < c->nx; x0 += pl.lx)
-      rows.push_back(Row{(int)s, x0, std::min(c->nx, x0 + pl.lx), 0, false});
+    for (int x0 = c->own0; x0 < c->own1; x0 += pl.lx)  // a slab's ghost planes are not updated
+      rows.push_back(Row{(int)s, x0, std::min(c->own1, x0 + pl.lx), 0, false});
   }
   {
     const long long tail = resident_ctas(pl, pl.tile, pl.stages, false);
@@ -631,6 +656,7 @@ static void build_lists(Plan& pl) {
           const int x = ps->base[(size_t)j * 3] + ((cc >> 2) & 1);
           const int y = ps->base[(size_t)j * 3 + 1] + ((cc >> 1) & 1);
           const int z = ps->base[(size_t)j * 3 + 2] + (cc & 1);
+          if (xrow[si][x] < 0) continue;  // a slab's ghost plane (a receiver corner)
           weight[xrow[si][x]][(size_t)(y / TY) * cols[si][1] + z / kTZ]++;
         }
   }
@@ -657,7 +683,9 @@ static void build_lists(Plan& pl) {
     }
   }
   const int U = (int)pl.units.size();
+  // unit of a node, -1 for a plane no unit updates (a slab's ghost planes)
   auto unit_of = [&](int s, int x, int y, int z) {
+    if (x < 0 || x >= (int)xrow[s].size() || xrow[s][x] < 0) return -1;
     const int ri = xrow[s][x];
     return fine[ri].base + pos[ri][(y / TY) * cols[s][1] + z / kTZ];
   };
@@ -686,13 +714,18 @@ static void build_lists(Plan& pl) {
           const int x = ip.base[(size_t)j * 3] + ((cc >> 2) & 1);
           const int y = ip.base[(size_t)j * 3 + 1] + ((cc >> 1) & 1);
           const int z = ip.base[(size_t)j * 3 + 2] + (cc & 1);
-          inj[std::make_tuple(unit_of((int)s, x, y, z), x, y, z)].push_back(InjTerm{j, w});
+          // only a slab's adjoint lists meet ghost planes here, and a slab
+          // has no adjoint step
+          const int un = unit_of((int)s, x, y, z);
+          if (un < 0) continue;
+          inj[std::make_tuple(un, x, y, z)].push_back(InjTerm{j, w});
         }
       if (role != kRoleRec) {
         const PointSet& sp = (role == kRoleAdj) ? c->src : c->rec;
         for (int j = 0; j < sp.n; ++j) {
           const int* b = &sp.base[(size_t)j * 3];
-          smp[unit_of((int)s, b[0], b[1], b[2])].push_back(j);
+          const int un = unit_of((int)s, b[0], b[1], b[2]);
+          if (un >= 0) smp[un].push_back(j);
         }
       }
     }
@@ -1320,6 +1353,11 @@ static void require_model(const fdw_ctx* c) {
   if (!c->model_set) fail(FDW_ERR_STATE, "model not set (fdw_set_model)");
 }
 
+// Whole time loops need every plane of the grid: a slab steps with fdw_step.
+static void require_whole(const fdw_ctx* c) {
+  if (c->slab) fail(FDW_ERR_STATE, "a slab context steps with fdw_step and exchanges ghost planes");
+}
+
 static void check_compatible(const std::vector<fdw_ctx*>& v) {
   const fdw_ctx* a = v[0];
   for (auto* c : v) {
@@ -1620,8 +1658,11 @@ double fdw_dt_max(int ndim, const double* spacing, int space_order, double vmax)
   return dt_limit(ndim, spacing, space_order, vmax);
 }
 
-fdw_status fdw_create(fdw_ctx** out, int ndim, const int64_t* shape, const double* spacing,
-                      int space_order, int nbl, double dt, int nt, double vmax, int device) {
+// A whole grid (x_end < 0) or the x slab [x_begin, x_end) of its computational
+// planes with r ghost planes on either side.
+static fdw_status create_ctx(fdw_ctx** out, int ndim, const int64_t* shape, const double* spacing,
+                             int space_order, int nbl, double dt, int nt, double vmax, int device,
+                             int64_t x_begin, int64_t x_end) {
   if (!out) return FDW_ERR_ARG;
   *out = nullptr;
   if (ndim != 2 && ndim != 3) return FDW_ERR_SHAPE;
@@ -1654,6 +1695,18 @@ fdw_status fdw_create(fdw_ctx** out, int ndim, const int64_t* shape, const doubl
     c->nt = nt;
     c->vmax = vmax;
     c->nx = (int)(c->phys[0] + 2 * nbl);
+    c->nx_full = c->nx;
+    c->own0 = 0;
+    c->own1 = c->nx;
+    if (x_end >= 0) {
+      if (x_begin < 0 || x_end > c->nx_full || x_end - x_begin < c->r)
+        fail(FDW_ERR_SHAPE, "slab planes outside the grid or fewer than r = order/2");
+      c->slab = true;
+      c->gx0 = (int)x_begin - c->r;
+      c->own0 = c->r;
+      c->own1 = c->r + (int)(x_end - x_begin);
+      c->nx = c->own1 + c->r;
+    }
     c->ny = ndim == 3 ? (int)(c->phys[1] + 2 * nbl) : 1;
     c->nz = (int)(c->phys[2] + 2 * nbl);
     c->nzp = (c->nz + 31) & ~31;
@@ -1668,7 +1721,8 @@ fdw_status fdw_create(fdw_ctx** out, int ndim, const int64_t* shape, const doubl
     size_t off = 0;
     for (int a = 0; a < 3; ++a) {
       const bool active = !(ndim == 2 && a == 1);
-      for (int i = 0; i < n3[a]; ++i) {
+      for (int il = 0; il < n3[a]; ++il) {
+        const long long i = a == 0 ? il + c->gx0 : il;  // index in the full grid
         double e = 0.0;
         if (active && nbl > 0) {
           const long long lo = nbl - i, hi = i - (nbl + c->phys[a] - 1);
@@ -1677,7 +1731,7 @@ fdw_status fdw_create(fdw_ctx** out, int ndim, const int64_t* shape, const doubl
           const double f = (double)d / nbl;
           e = emax * f * f;
         }
-        prof[off + i] = (float)(e * dt * 0.5);
+        prof[off + il] = (float)(e * dt * 0.5);
       }
       off += n3[a];
     }
@@ -1687,6 +1741,19 @@ fdw_status fdw_create(fdw_ctx** out, int ndim, const int64_t* shape, const doubl
   if (st != FDW_OK) return st;
   *out = c.release();
   return FDW_OK;
+}
+
+fdw_status fdw_create(fdw_ctx** out, int ndim, const int64_t* shape, const double* spacing,
+                      int space_order, int nbl, double dt, int nt, double vmax, int device) {
+  return create_ctx(out, ndim, shape, spacing, space_order, nbl, dt, nt, vmax, device, 0, -1);
+}
+
+fdw_status fdw_create_slab(fdw_ctx** out, int ndim, const int64_t* shape, const double* spacing,
+                           int space_order, int nbl, double dt, int nt, double vmax, int device,
+                           int64_t x_begin, int64_t x_end) {
+  if (x_end < 0) return FDW_ERR_SHAPE;
+  return create_ctx(out, ndim, shape, spacing, space_order, nbl, dt, nt, vmax, device, x_begin,
+                    x_end);
 }
 
 void fdw_destroy(fdw_ctx* ctx) {
@@ -1708,7 +1775,7 @@ fdw_status fdw_set_model(fdw_ctx* c, const float* m, int layout, int m_dtype, vo
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t n = layout == FDW_LAYOUT_PHYSICAL
                          ? (size_t)c->phys[0] * c->phys[1] * c->phys[2]
-                         : (size_t)c->nx * c->ny * c->nz;
+                         : (size_t)c->nx_full * c->ny * c->nz;
     const float* md = device_in(c, 7, m, n, s);
     if (m_dtype != c->mtype) {
       dfree(c->m);
@@ -1720,7 +1787,7 @@ fdw_status fdw_set_model(fdw_ctx* c, const float* m, int layout, int m_dtype, vo
     }
     CK(launch_model(md, layout == FDW_LAYOUT_PHYSICAL ? 0 : 1, (int)c->phys[0], (int)c->phys[1],
                     (int)c->phys[2], c->nbl, c->ndim, c->m, c->mtype,
-                    Geom{c->nx, c->ny, c->nz, c->nzp}, s));
+                    Geom{c->nx, c->ny, c->nz, c->nzp}, s, c->gx0, c->nx_full));
     c->model_set = true;
   });
 }
@@ -1741,8 +1808,9 @@ fdw_status fdw_set_damping(fdw_ctx* c, const float* eta, void* stream) {
       c->etaf = dalloc<float>((size_t)c->slot);
       CK(cudaMemsetAsync(c->etaf, 0, sizeof(float) * c->slot, s));
     }
-    const float* ed = device_in(c, 8, eta, (size_t)c->nx * c->ny * c->nz, s);
-    CK(launch_eta_field(ed, (float)(0.5 * c->dt), c->etaf, Geom{c->nx, c->ny, c->nz, c->nzp}, s));
+    const float* ed = device_in(c, 8, eta, (size_t)c->nx_full * c->ny * c->nz, s);
+    CK(launch_eta_field(ed, (float)(0.5 * c->dt), c->etaf, Geom{c->nx, c->ny, c->nz, c->nzp}, s,
+                        c->gx0, c->nx_full));
     if (!c->use_etaf) {
       c->use_etaf = true;
       c->buffers_version++;
@@ -1754,7 +1822,7 @@ fdw_status fdw_set_sources(fdw_ctx* c, int nsrc, const double* xyz) {
   if (!c) return FDW_ERR_ARG;
   return guard(&c->err, [&] {
     set_device(c->device);
-    compute_points(c, c->src, nsrc, xyz);
+    compute_points(c, c->src, nsrc, xyz, false);
     dfree(c->qsave);
     c->qsave = nullptr;
     c->have_ckpt = false;
@@ -1765,7 +1833,7 @@ fdw_status fdw_set_receivers(fdw_ctx* c, int nrec, const double* xyz) {
   if (!c) return FDW_ERR_ARG;
   return guard(&c->err, [&] {
     set_device(c->device);
-    compute_points(c, c->rec, nrec, xyz);
+    compute_points(c, c->rec, nrec, xyz, true);
   });
 }
 
@@ -1773,6 +1841,7 @@ fdw_status fdw_forward(fdw_ctx* c, const float* q, float* rec, void* stream) {
   if (!c) return FDW_ERR_ARG;
   return guard(&c->err, [&] {
     require_model(c);
+    require_whole(c);
     set_device(c->device);
     Plan& pl = ctx_plan(c);
     plan_forward(pl, &q, &rec, 0, 0, static_cast<cudaStream_t>(stream));
@@ -1783,6 +1852,7 @@ fdw_status fdw_forward_ckpt(fdw_ctx* c, const float* q, float* rec, int k, int s
   if (!c) return FDW_ERR_ARG;
   return guard(&c->err, [&] {
     require_model(c);
+    require_whole(c);
     if (k < 1) fail(FDW_ERR_ARG, "ckpt_every must be >= 1");
     if (stype != kF32 && stype != kF16 && stype != kBF16) fail(FDW_ERR_ARG, "bad snapshot type");
     set_device(c->device);
@@ -1796,6 +1866,7 @@ fdw_status fdw_adjoint(fdw_ctx* c, const float* d, float* qadj, void* stream) {
   if (!c) return FDW_ERR_ARG;
   return guard(&c->err, [&] {
     require_model(c);
+    require_whole(c);
     set_device(c->device);
     if (!c->lam) {
       c->lam = dalloc<float>((size_t)c->slot * 2);
@@ -1823,10 +1894,99 @@ fdw_status fdw_gradient(fdw_ctx* c, const float* resid, const float* resid_sub, 
   if (!c) return FDW_ERR_ARG;
   return guard(&c->err, [&] {
     require_model(c);
+    require_whole(c);
     if (layout != FDW_LAYOUT_PHYSICAL && layout != FDW_LAYOUT_COMPUTATIONAL) fail(FDW_ERR_ARG, "bad layout");
     set_device(c->device);
     Plan& pl = ctx_plan(c);
     plan_gradient(pl, &resid, &resid_sub, &grad, layout, static_cast<cudaStream_t>(stream));
+  });
+}
+
+fdw_status fdw_step(fdw_ctx* c, int n, const float* q, float* rec, void* stream) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    require_model(c);
+    if (n < 0 || n > c->nt - 1) fail(FDW_ERR_ARG, "step index outside 0 .. nt-1");
+    if (c->src.n > 0 && !(q && is_device_ptr(q))) fail(FDW_ERR_ARG, "q must be a device array");
+    if (c->rec.n > 0 && !(rec && is_device_ptr(rec)))
+      fail(FDW_ERR_ARG, "rec must be a device array");
+    set_device(c->device);
+    Plan& pl = ctx_plan(c);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n == 0) CK(cudaMemsetAsync(c->u, 0, sizeof(float) * 2 * c->slot, s));
+    pl.hdesc[kRoleFwd][0].inj_a = q;
+    pl.hdesc[kRoleFwd][0].inj_b = nullptr;
+    pl.hdesc[kRoleFwd][0].smp_out = rec;
+    upload_desc(pl, kRoleFwd, s);
+    if (n == c->nt - 1) {  // the last time level: samples only
+      if (c->rec.n > 0) CK(launch_sample(pl.d_desc[kRoleFwd], 1, c->rec.n, n & 1, n, s));
+      c->fwd_done = true;
+      return;
+    }
+    reset_tickets(pl, s);
+    int flags = 0;
+    if (c->src.n > 0) flags |= kInject;
+    if (c->rec.n > 0) flags |= kSample;
+    StepArgs a{kRoleFwd, n & 1, (n + 1) & 1, (n + 1) & 1, 0, n, n, flags, false};
+    launch_step(pl, a, s);
+  });
+}
+
+fdw_status fdw_halo_planes(fdw_ctx* c, int n, float** send_lo, float** send_hi, float** recv_lo,
+                           float** recv_hi, int64_t* count) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    if (!c->slab) fail(FDW_ERR_ARG, "not a slab context");
+    if (n < 0 || n > c->nt - 2) fail(FDW_ERR_ARG, "step index outside 0 .. nt-2");
+    if (!send_lo || !send_hi || !recv_lo || !recv_hi || !count) fail(FDW_ERR_ARG, "null output");
+    float* base = c->u + (size_t)((n + 1) & 1) * c->slot;  // u^{n+1}
+    const size_t plane = (size_t)c->ny * c->nzp;
+    *send_lo = base + (size_t)c->own0 * plane;
+    *send_hi = base + (size_t)(c->own1 - c->r) * plane;
+    *recv_lo = base + (size_t)(c->own0 - c->r) * plane;
+    *recv_hi = base + (size_t)c->own1 * plane;
+    *count = (int64_t)(c->r * plane);
+  });
+}
+
+fdw_status fdw_exchange_ghosts(fdw_ctx* lower, fdw_ctx* upper, int n, void* stream) {
+  if (!lower || !upper || lower == upper) return FDW_ERR_ARG;
+  return guard(&upper->err, [&] {
+    if (!lower->slab || !upper->slab) fail(FDW_ERR_ARG, "not slab contexts");
+    if (lower->gx0 + lower->own1 != upper->gx0 + upper->own0 || lower->ny != upper->ny ||
+        lower->nzp != upper->nzp || lower->r != upper->r)
+      fail(FDW_ERR_ARG, "the slabs are not neighbours of one grid");
+    float *sl0, *sh0, *rl0, *rh0, *sl1, *sh1, *rl1, *rh1;
+    int64_t cnt = 0;
+    if (fdw_halo_planes(lower, n, &sl0, &sh0, &rl0, &rh0, &cnt) != FDW_OK ||
+        fdw_halo_planes(upper, n, &sl1, &sh1, &rl1, &rh1, &cnt) != FDW_OK)
+      fail(FDW_ERR_ARG, "step index outside 0 .. nt-2");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = sizeof(float) * (size_t)cnt;
+    set_device(upper->device);
+    CK(cudaMemcpyPeerAsync(rl1, upper->device, sh0, lower->device, bytes, s));
+    CK(cudaMemcpyPeerAsync(rh0, lower->device, sl1, upper->device, bytes, s));
+  });
+}
+
+fdw_status fdw_halo_copy(fdw_ctx* c, int n, int dir, float* lo, float* hi, void* stream) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    if (dir != 0 && dir != 1) fail(FDW_ERR_ARG, "dir must be 0 (get) or 1 (put)");
+    float *sl, *sh, *rl, *rh;
+    int64_t cnt = 0;
+    if (fdw_halo_planes(c, n, &sl, &sh, &rl, &rh, &cnt) != FDW_OK)
+      fail(FDW_ERR_ARG, "not a slab context or step index outside 0 .. nt-2");
+    set_device(c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = sizeof(float) * (size_t)cnt;
+    if (dir == 0) {
+      if (lo) CK(cudaMemcpyAsync(lo, sl, bytes, cudaMemcpyDefault, s));
+      if (hi) CK(cudaMemcpyAsync(hi, sh, bytes, cudaMemcpyDefault, s));
+    } else {
+      if (lo) CK(cudaMemcpyAsync(rl, lo, bytes, cudaMemcpyDefault, s));
+      if (hi) CK(cudaMemcpyAsync(rh, hi, bytes, cudaMemcpyDefault, s));
+    }
   });
 }
 
@@ -1919,6 +2079,7 @@ fdw_status fdw_batch_create(fdw_batch** out, int nshots, fdw_ctx* const* ctxs) {
   fdw_status st = guard(&b->err, [&] {
     for (int i = 0; i < nshots; ++i) {
       if (!ctxs[i]) fail(FDW_ERR_ARG, "null context in batch");
+      if (ctxs[i]->slab) fail(FDW_ERR_ARG, "slab contexts cannot be batched");
       b->shots.push_back(ctxs[i]);
     }
     check_compatible(b->shots);

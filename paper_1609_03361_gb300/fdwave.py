@@ -81,6 +81,13 @@ _SIGS = [
                                 _D, _I, _D, _P, _I, _P, _P, _I, _P, _P, _P]),
     ("fdw_diffusion2d", _I, [_P, _P, ctypes.c_int64, ctypes.c_int64, _D, _D, _D, _D, _I, _I, _P]),
     ("fdw_set_checkpoint_budget", _I, [_P, _I]),
+    ("fdw_create_slab", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(ctypes.c_int64),
+                             ctypes.POINTER(_D), _I, _I, _D, _I, _D, _I, ctypes.c_int64,
+                             ctypes.c_int64]),
+    ("fdw_step", _I, [_P, _I, _P, _P, _P]),
+    ("fdw_halo_planes", _I, [_P, _I, _PP, _PP, _PP, _PP, ctypes.POINTER(ctypes.c_int64)]),
+    ("fdw_exchange_ghosts", _I, [_P, _P, _I, _P]),
+    ("fdw_halo_copy", _I, [_P, _I, _I, _P, _P, _P]),
     ("fdw_checkpoint_schedule", _I, [_I, _I, ctypes.POINTER(_I), _I]),
 ]
 
@@ -188,6 +195,43 @@ def fdw_create(shape, spacing, space_order, nbl, dt, nt, vmax, device=0):
                             int(space_order), int(nbl), float(dt), int(nt), float(vmax),
                             int(device)))
     return out.value
+
+
+def fdw_create_slab(shape, spacing, space_order, nbl, dt, nt, vmax, device, x_begin, x_end):
+    ndim = len(shape)
+    sh = (ctypes.c_int64 * ndim)(*[int(s) for s in shape])
+    sp = np.broadcast_to(np.asarray(spacing, dtype=np.float64), (ndim,)).copy()
+    out = _P()
+    _check(lib().fdw_create_slab(ctypes.byref(out), ndim, sh, sp.ctypes.data_as(ctypes.POINTER(_D)),
+                                 int(space_order), int(nbl), float(dt), int(nt), float(vmax),
+                                 int(device), int(x_begin), int(x_end)))
+    return out.value
+
+
+def fdw_step(ctx, n, q, rec, stream=None, device=0):
+    keep = []
+    _check(lib().fdw_step(ctx, int(n), _ptr(q, keep), _ptr(rec, keep), _stream(stream, device)),
+           ctx)
+
+
+def fdw_halo_planes(ctx, n):
+    """(send_lo, send_hi, recv_lo, recv_hi, count): device addresses and float
+    count of the ghost-plane blocks of a slab after step n."""
+    ptrs = [_P() for _ in range(4)]
+    cnt = ctypes.c_int64()
+    _check(lib().fdw_halo_planes(ctx, int(n), *[ctypes.byref(p) for p in ptrs], ctypes.byref(cnt)),
+           ctx)
+    return tuple(p.value for p in ptrs) + (cnt.value,)
+
+
+def fdw_exchange_ghosts(lower, upper, n, stream=None, device=0):
+    _check(lib().fdw_exchange_ghosts(lower, upper, int(n), _stream(stream, device)), upper)
+
+
+def fdw_halo_copy(ctx, n, direction, lo, hi, stream=None, device=0):
+    keep = []
+    _check(lib().fdw_halo_copy(ctx, int(n), int(direction), _ptr(lo, keep), _ptr(hi, keep),
+                               _stream(stream, device)), ctx)
 
 
 def fdw_destroy(ctx):
@@ -374,14 +418,20 @@ class Solver:
     """One shot on one GPU.  Arrays may be numpy (host) or torch tensors (host or
     CUDA); outputs are allocated like the first array argument of the call."""
 
-    def __init__(self, shape, spacing, space_order, nbl, dt, nt, vmax, device=0):
+    def __init__(self, shape, spacing, space_order, nbl, dt, nt, vmax, device=0, slab=None):
+        """slab = (x_begin, x_end): only those computational x planes (fdw_create_slab)."""
         self.shape = tuple(int(s) for s in shape)
         self.ndim = len(self.shape)
         self.spacing = tuple(np.broadcast_to(np.asarray(spacing, dtype=np.float64),
                                              (self.ndim,)).tolist())
         self.space_order, self.nbl, self.dt, self.nt = int(space_order), int(nbl), float(dt), int(nt)
         self.vmax, self.device = float(vmax), int(device)
-        self.ctx = fdw_create(self.shape, self.spacing, space_order, nbl, dt, nt, vmax, device)
+        self.slab = None if slab is None else (int(slab[0]), int(slab[1]))
+        if self.slab is None:
+            self.ctx = fdw_create(self.shape, self.spacing, space_order, nbl, dt, nt, vmax, device)
+        else:
+            self.ctx = fdw_create_slab(self.shape, self.spacing, space_order, nbl, dt, nt, vmax,
+                                       device, *self.slab)
         self.nsrc = 0
         self.nrec = 0
 
@@ -398,7 +448,13 @@ class Solver:
 
     @property
     def comp_shape(self):
-        return tuple(n + 2 * self.nbl for n in self.shape)
+        """Shape of the computational arrays of this context (for a slab: its
+        own planes plus r ghost planes on either side, in x)."""
+        full = tuple(n + 2 * self.nbl for n in self.shape)
+        if self.slab is None:
+            return full
+        r = self.space_order // 2
+        return (self.slab[1] - self.slab[0] + 2 * r,) + full[1:]
 
     def _like(self, ref, shape):
         if _is_tensor(ref):
@@ -458,6 +514,13 @@ class Solver:
 
     def autotune(self, steps=10):
         fdw_autotune(self.ctx, steps)
+
+    def step(self, n, q, rec, stream=None):
+        """One time step (device arrays q [nt][nsrc], rec [nt][nrec])."""
+        fdw_step(self.ctx, n, q, rec, stream, self.device)
+
+    def halo_planes(self, n):
+        return fdw_halo_planes(self.ctx, n)
 
     def set_checkpoint_budget(self, max_pairs):
         fdw_set_checkpoint_budget(self.ctx, max_pairs)
