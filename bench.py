@@ -310,6 +310,7 @@ def run_forward(args, world, rank, local):
         extras["batched"] = run_batched(args.batch_shots, 800, dev)
         extras["fwi"] = run_fwi(args.fwi_shots, args.fwi_nt, 10, dev)
         extras["diffusion"] = run_diffusion(dev)
+        extras["decomposition"] = run_decomp(dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GPts/s", "n_gpus": world,
@@ -386,6 +387,63 @@ def run_diffusion(dev):
     del u0
     torch.cuda.empty_cache()
     return out
+
+
+def run_decomp(dev, nt=200, nparts=2):
+    """Single-shot domain decomposition on this one GPU: the 256^3 SO8 shot cut
+    into x slabs held by one process (ghost planes exchanged by device copies
+    after every step), against the whole grid stepped the same way (one host
+    call per step, no CUDA graph).  On one GPU the slabs share the device, so
+    this measures the cost of the decomposition (exchange, smaller launches),
+    not a speed-up."""
+    import torch
+    from paper_1609_03361_gb300 import fdwave as fw
+    from paper_1609_03361_gb300.decomp import SlabForward
+    w = cfg2_workload(nt)
+    pts = int(np.prod(w.comp_shape))
+    q = torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev)
+    m = torch.from_numpy(w.m.astype(np.float32)).to(dev)
+    nrec = w.rec.shape[0]
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(run):
+        run()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+
+    s = fw.Solver(w.shape, w.spacing, w.space_order, w.nbl, w.dt, nt, w.vmax,
+                  device=dev.index or 0)
+    s.set_model(m)
+    s.set_sources(w.src)
+    s.set_receivers(w.rec)
+    rec = torch.zeros((nt, nrec), device=dev)
+
+    def whole():
+        for n in range(nt):
+            s.step(n, q, rec)
+    ms_whole = timed(whole)
+    sf = SlabForward(w.shape, w.spacing, w.space_order, w.nbl, w.dt, nt, w.vmax, nparts,
+                     devices=[dev.index or 0] * nparts)
+    sf.set_model(m)
+    sf.set_sources(w.src)
+    sf.set_receivers(w.rec)
+    recs = [torch.zeros((nt, nrec), device=dev) for _ in range(nparts)]
+    ms_slabs = timed(lambda: sf.forward([q] * nparts, recs))
+    same = bool(torch.equal(sum(recs), rec))
+    halo = fw.fdw_halo_planes(sf.slabs[0].ctx, 0)[4] * 4
+    sf.close()
+    s.close()
+    return {"workload": f"256^3 SO8 shot, {nt} steps, {nparts} x slabs on one GPU",
+            "gpts_whole_stepwise": pts * (nt - 1) / (ms_whole * 1e-3) / 1e9,
+            "gpts_slabs": pts * (nt - 1) / (ms_slabs * 1e-3) / 1e9,
+            "exchange_bytes_per_step": 2 * (nparts - 1) * halo,
+            "traces_identical": same}
 
 
 def run_batched(nshots, nt, dev, timed_reps=1):
@@ -693,7 +751,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="forward",
-                    choices=["forward", "so16", "precision", "diffusion", "fwi"])
+                    choices=["forward", "so16", "precision", "diffusion", "fwi", "decomp"])
     ap.add_argument("--nt", type=int, default=1000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -719,6 +777,8 @@ def main():
         if rank == 0:
             if args.workload == "diffusion":
                 print(json.dumps(run_diffusion(dev)), flush=True)
+            elif args.workload == "decomp":
+                print(json.dumps(run_decomp(dev)), flush=True)
             elif args.workload == "fwi":
                 print(json.dumps(run_fwi(args.fwi_shots, args.fwi_nt, 10, dev)), flush=True)
             else:
