@@ -365,3 +365,51 @@ def test_batched_config_full_grids_first_steps(fw):
                              qs[i].cpu().numpy().astype(np.float64), w.rec)
         assert np.abs(ref).max() > 0
         assert rel_l2(recs[i], ref) < TOL
+
+
+@pytest.mark.parametrize("shape,p,nbl", [((2, 2, 2), 16, 0), ((3, 2, 5), 8, 1), ((2, 3), 16, 0),
+                                         ((5, 4, 3), 2, 0)])
+def test_tiny_grids(fw, shape, p, nbl):
+    """Grids smaller than the stencil and the tile: every neighbour beyond the
+    grid is the zero halo."""
+    pb = Problem(shape, 10.0, p, nbl, 12, nsrc=1, nrec=2, seed=len(shape) + p)
+    rec, u = _fwd(fw, pb)
+    ref, uref = pb.oracle_forward(final=True)
+    assert rel_l2(rec, ref) < TOL
+    assert rel_l2(u, uref) < TOL
+
+
+def test_single_step(fw):
+    pb = Problem((20, 18, 22), 10.0, 8, 4, 2, nsrc=2, nrec=5, seed=4)
+    rec, u = _fwd(fw, pb)
+    ref, uref = pb.oracle_forward(final=True)
+    assert rel_l2(u, uref) < TOL
+    assert np.allclose(rec, ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+
+
+def test_config_3d_512_so16_full_grid_first_steps(fw):
+    """The 512^3 SO16 workload on its full 592^3 computational grid (830 MB a
+    field) over its first 8 steps, FP32 model, against the oracle."""
+    import oracle
+    from paper_1609_03361_gb300 import workloads as W
+    nt = 8
+    w = W.config_3d(512, 12.5, 16, nt)
+    w.dt = W.choose_dt(oracle.dt_max(3, w.spacing, 16, w.vmax))
+    dev = torch.device("cuda", 0)
+    s = fw.Solver(w.shape, w.spacing, 16, w.nbl, w.dt, nt, w.vmax)
+    s.set_model(torch.from_numpy(w.m.astype(np.float32)).to(dev))
+    s.set_sources(w.src)
+    s.set_receivers(w.rec)
+    q32 = w.wavelet().astype(np.float32)[:, None]
+    rec = s.forward(torch.from_numpy(q32).to(dev)).cpu().numpy()
+    u = s.wavefield(0, like=torch.from_numpy(q32).to(dev)).cpu().numpy()
+    s.sync()
+    s.close()
+    st = oracle.Setup(w.shape, w.spacing, 16, w.nbl, w.dt, nt)
+    M = oracle.extend_model(st, w.m.astype(np.float32).astype(np.float64))
+    ref, uref = oracle.forward(st, M, oracle.damping(st, w.vmax), w.src, q32.astype(np.float64),
+                               w.rec, final=True)
+    assert np.abs(uref).max() > 0
+    assert rel_l2(u, uref) < TOL
+    if np.abs(ref).max() > 0:
+        assert rel_l2(rec, ref) < TOL
