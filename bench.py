@@ -306,7 +306,7 @@ def run_forward(args, world, rank, local):
         base = cpu_baseline(w)
 
     extras = {}
-    if not args.no_extras:
+    if not args.no_extras and world == 1:   # single-GPU measurements: once, at N = 1
         extras["batched"] = run_batched(args.batch_shots, 800, dev)
         extras["fwi"] = run_fwi(args.fwi_shots, args.fwi_nt, 10, dev)
         extras["diffusion"] = run_diffusion(dev)
