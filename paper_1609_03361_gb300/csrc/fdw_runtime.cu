@@ -1585,7 +1585,7 @@ static void plan_autotune(Plan& pl, int steps) {
     std::vector<std::tuple<float, int, int, int>> cand;
     for (int t : tiles) {
       const int ms = max_stages(pl, t);
-      for (int extra : {2, 3}) {
+      for (int extra : {1, 2, 3}) {
         const int st = std::min(pl.r + 1 + extra, ms);
         for (int lx : lxs) {
           if (lx > nxmax && lx != nxmax) continue;
