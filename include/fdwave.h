@@ -214,8 +214,8 @@ fdw_status fdw_set_checkpoint_budget(fdw_ctx* ctx, int max_pairs);
  * nslots < 0, cap < 0 or actions NULL with cap > 0.  Host only. */
 int fdw_checkpoint_schedule(int nseg, int nslots, int* actions, int cap);
 
-/* Force a tile configuration: tile index (0..5, -1 = default; 3 is meant for
- * 2D grids), x-chunk length (0 = default) and pipeline depth of the forward
+/* Force a tile configuration: tile index (0..6, -1 = default; 3 is meant for
+ * 2D grids, 6 keeps per-plane tiles in a second ring), x-chunk length (0 = default) and pipeline depth of the forward
  * and adjoint steps (>= r + 2 with r = space_order / 2, 0 = default; the
  * gradient step picks its own).  FDW_ERR_ARG outside these ranges. */
 fdw_status fdw_set_tiling(fdw_ctx* ctx, int tile, int xchunk, int stages);

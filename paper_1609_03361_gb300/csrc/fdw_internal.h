@@ -13,12 +13,18 @@ namespace fdw {
 // NY consecutive rows and each lane four z points, so a tile is (4 * BY * NY) x 32
 // points in (y, z).  Tiles 0 and 2 unroll the x loop so the register queue
 // rotates; the others shift it (smaller code).  Tile 3 is meant for 2D grids.
+// Tile 6 is tile 4 with the per-plane tiles in a second ring: less shared
+// memory per CTA, which lets the high orders (r >= 6) hold three CTAs per SM.
 struct TileShape {
   int ny_pts;
   int warps;
+  bool split;  // the forward and adjoint steps also keep the per-plane tiles
+               // in a second ring (gradient steps always do)
 };
-constexpr int kNumTiles = 6;
-constexpr TileShape kTiles[kNumTiles] = {{1, 4}, {2, 4}, {1, 8}, {1, 1}, {1, 4}, {2, 2}};
+constexpr int kNumTiles = 7;
+constexpr TileShape kTiles[kNumTiles] = {{1, 4, false}, {2, 4, false}, {1, 8, false},
+                                         {1, 1, false}, {1, 4, false}, {2, 2, false},
+                                         {1, 4, true}};
 constexpr int tile_rows(const TileShape& t) { return 4 * t.ny_pts * t.warps; }
 
 // Kernel registry: one translation unit per stencil radius.

@@ -495,7 +495,7 @@ static int second_ring_stages(const StageLayout& L, int stages) {
 }
 
 static StageLayout stage_layout(int r, int tile, int mt_bytes, bool grad, bool etaf) {
-  const bool split = grad;  // a second ring measured slower for the forward step
+  const bool split = grad || kTiles[tile].split;
   const int TY = tile_rows(kTiles[tile]);
   const int R4 = (r + 3) & ~3;
   const int ZW = kTZ + 2 * R4, YW = TY + 2 * r;
@@ -1522,7 +1522,7 @@ static void plan_autotune(Plan& pl, int steps) {
       if (c->ny > 1) all2d = false;
       nxmax = std::max(nxmax, c->nx);
     }
-    std::vector<int> tiles = all2d ? std::vector<int>{3} : std::vector<int>{0, 1, 2, 4, 5};
+    std::vector<int> tiles = all2d ? std::vector<int>{3} : std::vector<int>{0, 1, 2, 4, 5, 6};
     std::vector<int> lxs = {16, 32, 48, 64, 80, 96, 128, nxmax};
     cudaStream_t s = pl.cap;
     cudaEvent_t e0, e1;

@@ -360,8 +360,12 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
   return true;
 }
 
+// The forward step with a second ring at radius 7 and 8 asks for three
+// resident CTAs per SM (136 registers a thread), which its smaller shared
+// memory allows; every other instance leaves the register count to the
+// compiler (a minimum of 0 blocks states no constraint).
 template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT = GRAD>
-__global__ void __launch_bounds__((BY + 1) * 32)
+__global__ void __launch_bounds__((BY + 1) * 32, (SPLIT && !GRAD && R >= 7) ? 3 : 0)
 step_kernel(const __grid_constant__ StepParams P) {
   constexpr int TZ = kTZ;
   constexpr int TY = 4 * BY * NY;

@@ -18,6 +18,8 @@ const void* step_kernel_r6(int tile, bool grad) {
                           : (const void*)&step_kernel<6, 1, 4, false, false>;
     case 5: return grad ? (const void*)&step_kernel<6, 2, 2, true, false>
                           : (const void*)&step_kernel<6, 2, 2, false, false>;
+    case 6: return grad ? (const void*)&step_kernel<6, 1, 4, true, false>
+                          : (const void*)&step_kernel<6, 1, 4, false, false, true>;
     default: return nullptr;
   }
 }
