@@ -147,6 +147,21 @@ def cfg2_workload(nt=1000):
     return w
 
 
+def cpu_model():
+    """Host CPU description for the baseline records (best effort)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        for key in ("model name", "Model name", "CPU part"):
+            for line in txt.splitlines():
+                if line.startswith(key):
+                    return f"{key}: {line.split(':', 1)[1].strip()}"
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(w, target_s=15.0):
     """FP64 oracle on the host cores: the full computational grid for a few
     time steps, GPts/s (test infrastructure, timed as it stands)."""
@@ -169,6 +184,7 @@ def cpu_baseline(w, target_s=15.0):
     if os.environ.get("OMP_NUM_THREADS"):
         cores = min(cores, int(os.environ["OMP_NUM_THREADS"]))
     return {"value": pts * (nts - 1) / el / 1e9, "unit": "GPts/s", "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(),
             "sample": f"{w.comp_shape[0]}^3 computational grid, {nts - 1} FP64 time steps "
                       f"({el:.1f} s), same model/source/receivers"}
 
@@ -276,6 +292,7 @@ def run_forward(args, world, rank, local):
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "frac_of_nominal_7900": achieved / 7900.0,
                 "bytes_per_point": B_ALG, "points_per_launch": pts}
 
     # end to end through the public API with pinned host buffers
