@@ -222,6 +222,7 @@ def run_reference(args, world, rank):
             "config": {"workload": "3D acoustic forward 256^3 (336^3 computational), SO8, FP64 "
                                    f"oracle sample of {nts - 1} time steps per step"},
             "cpu_baseline": {"value": value, "unit": "GPts/s", "cores": cores, "kind": "oracle",
+                             "cpu": cpu_model(),
                              "sample": f"{nts - 1} time steps of the full 336^3 grid per step"},
             "e2e": {"value": value, "unit": "GPts/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
