@@ -545,24 +545,55 @@ step_kernel(const __grid_constant__ StepParams P) {
         const float* B = (P.flags & kInjectDiff) ? d->inj_b + (long long)P.inj_row * d->inj_ld
                                                  : nullptr;
         float* uo = d->u + (long long)P.out * d->uslot;
-        for (int i = ib + tid; i < ie; i += NCONS) {
-          const InjNode nd = P.inj_nodes[i];
+        const InjNode* nodes = P.inj_nodes;
+        const InjTerm* terms = P.inj_terms;
+        const void* mp = d->m;
+        const float* eta = d->eta;
+        const float* etafp = d->etaf;
+        float* accp = d->acc;
+        const float* fwdp = GRAD ? d->fwd + (long long)P.fslot * d->fslot : nullptr;
+        auto node_sum = [&](const InjNode& nd) {
           float sum = 0.f;
           for (int t = nd.tbeg; t < nd.tend; ++t) {
-            const InjTerm tm = P.inj_terms[t];
+            const InjTerm tm = terms[t];
             const float v = B ? A[tm.j] - B[tm.j] : A[tm.j];
             sum = fmaf(tm.w, v, sum);
           }
-          const long long off = ((long long)nd.x * ny + nd.y) * nzp + nd.z;
-          const float s = load_m(d->m, mtype, off);
-          const float e = etaf ? d->etaf[off]
-                               : d->eta[nd.x] + d->eta[nx + nd.y] + d->eta[nx + ny + nd.z];
-          // dt^2 q / (m + eta dt/2) with s = 1/m
-          const float delta = P.dt2 * sum * s / (1.f + e * s);
-          const float nv = uo[off] + delta;
-          uo[off] = nv;
-          tmax = fmaxf(tmax, fabsf(nv));
-          if (GRAD) d->acc[off] = fmaf(d->fwd[(long long)P.fslot * d->fslot + off], delta, d->acc[off]);
+          return sum;
+        };
+        // dt^2 q / (m + eta dt/2) with s = 1/m, at node nd
+        auto node_delta = [&](const InjNode& nd, long long off, float sum) {
+          const float s = load_m(mp, mtype, off);
+          const float e = etaf ? etafp[off] : eta[nd.x] + eta[nx + nd.y] + eta[nx + ny + nd.z];
+          return P.dt2 * sum * s / (1.f + e * s);
+        };
+        // two nodes per pass: their independent loads overlap (receiver
+        // residuals in the adjoint step put about a thousand nodes in a unit)
+        for (int i = ib + tid; i < ie; i += 2 * NCONS) {
+          const int i2 = i + NCONS;
+          const bool two = i2 < ie;
+          const InjNode n1 = nodes[i];
+          const InjNode n2 = nodes[two ? i2 : i];
+          const long long off1 = ((long long)n1.x * ny + n1.y) * nzp + n1.z;
+          const long long off2 = ((long long)n2.x * ny + n2.y) * nzp + n2.z;
+          const float d1 = node_delta(n1, off1, node_sum(n1));
+          const float d2 = node_delta(n2, off2, node_sum(n2));
+          const float u1 = uo[off1], u2 = uo[off2];
+          float f1 = 0.f, f2 = 0.f, a1 = 0.f, a2 = 0.f;
+          if (GRAD) {
+            f1 = fwdp[off1];
+            f2 = fwdp[off2];
+            a1 = accp[off1];
+            a2 = accp[off2];
+          }
+          uo[off1] = u1 + d1;
+          tmax = fmaxf(tmax, fabsf(u1 + d1));
+          if (GRAD) accp[off1] = fmaf(f1, d1, a1);
+          if (two) {
+            uo[off2] = u2 + d2;
+            tmax = fmaxf(tmax, fabsf(u2 + d2));
+            if (GRAD) accp[off2] = fmaf(f2, d2, a2);
+          }
         }
       }
       if (P.flags & kAbsMax) {
