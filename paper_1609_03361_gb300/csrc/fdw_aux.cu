@@ -12,6 +12,7 @@
 
 #include <algorithm>
 
+#include "fdw_device.cuh"
 #include "fdw_internal.h"
 
 namespace fdw {
@@ -210,6 +211,36 @@ __global__ void copy32_kernel(const AuxShot* shots, int dir) {
   }
 }
 
+// Injection of one step's data into u^{n+1} as a launch of its own (the
+// adjoint step's receiver residuals: thousands of nodes, which spread over
+// every SM here instead of queueing at the tails of the few units that hold
+// them).  Per node the same arithmetic as the step kernel's unit tail:
+// u^{n+1} += dt^2 sum_t w_t a_j / (m + eta dt/2) with s = 1/m, and with grad
+// the accumulator's share fwd * delta.  Nodes are unique, so no atomics.
+__global__ void inject_kernel(const ShotDesc* shots, const InjNode* nodes, const int* node_shot,
+                              const InjTerm* terms, int nnodes, int row, int out, int fslot,
+                              float dt2, int diff, int grad, int etaf) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nnodes; i += gridDim.x * blockDim.x) {
+    const InjNode nd = nodes[i];
+    const ShotDesc& d = shots[node_shot[i]];
+    const float* A = d.inj_a + (long long)row * d.inj_ld;
+    const float* B = diff ? d.inj_b + (long long)row * d.inj_ld : nullptr;
+    float sum = 0.f;
+    for (int t = nd.tbeg; t < nd.tend; ++t) {
+      const InjTerm tm = terms[t];
+      const float v = B ? A[tm.j] - B[tm.j] : A[tm.j];
+      sum = fmaf(tm.w, v, sum);
+    }
+    const long long off = ((long long)nd.x * d.ny + nd.y) * d.nzp + nd.z;
+    const float sv = load_m(d.m, d.mtype, off);
+    const float e = etaf ? d.etaf[off] : d.eta[nd.x] + d.eta[d.nx + nd.y] + d.eta[d.nx + d.ny + nd.z];
+    const float delta = dt2 * sum * sv / (1.f + e * sv);
+    float* uo = d.u + (long long)out * d.uslot;
+    uo[off] = uo[off] + delta;
+    if (grad) d.acc[off] = fmaf(d.fwd[(long long)fslot * d.fslot + off], delta, d.acc[off]);
+  }
+}
+
 // Gradient output.  layout 1: computational shape, out = scale * acc.
 // layout 0: physical shape, each physical cell sums the computational cells
 // whose clamped index is that cell (the adjoint of the edge extension).
@@ -308,6 +339,16 @@ cudaError_t launch_unpack(const AuxShot* shots, int nshots, long long maxn, int 
   if (stype == kF16) unpack16_kernel<__half><<<g, kThreads, 0, s>>>(shots);
   else if (stype == kBF16) unpack16_kernel<__nv_bfloat16><<<g, kThreads, 0, s>>>(shots);
   else copy32_kernel<<<g, kThreads, 0, s>>>(shots, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inject(const ShotDesc* shots, const InjNode* nodes, const int* node_shot,
+                          const InjTerm* terms, int nnodes, int row, int out, int fslot, float dt2,
+                          bool diff, bool grad, bool etaf, cudaStream_t s) {
+  if (nnodes <= 0) return cudaSuccess;
+  const int blocks = std::min((nnodes + kThreads - 1) / kThreads, 152 * 8);
+  inject_kernel<<<blocks, kThreads, 0, s>>>(shots, nodes, node_shot, terms, nnodes, row, out, fslot,
+                                            dt2, diff ? 1 : 0, grad ? 1 : 0, etaf ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -70,6 +70,11 @@ cudaError_t launch_grad_out(const float* acc, Geom g, float scale, float* out, i
                             int nbl, int ndim, int phys_x, int phys_y, int phys_z,
                             cudaStream_t s);
 cudaError_t launch_copy_out(const float* field, Geom g, float* out, cudaStream_t s);
+// One step's injection as its own launch (see fdw_aux.cu): node_shot[i] is
+// the shot of nodes[i]; out / fslot the wavefield and forward-field slots.
+cudaError_t launch_inject(const ShotDesc* shots, const InjNode* nodes, const int* node_shot,
+                          const InjTerm* terms, int nnodes, int row, int out, int fslot, float dt2,
+                          bool diff, bool grad, bool etaf, cudaStream_t s);
 
 // Binomial checkpoint schedules over the segments of the gradient pass
 // (fdw_revolve.cu).

@@ -263,16 +263,19 @@ struct fdw_ctx {
 enum Role { kRoleFwd = 0, kRoleAdj = 1, kRoleRec = 2, kNumRoles = 3 };
 
 struct RoleLists {
-  std::vector<int> inj_ptr, smp_ptr, smp_pts;
+  std::vector<int> inj_ptr, smp_ptr, smp_pts, node_shot;
   std::vector<InjNode> nodes;
   std::vector<InjTerm> terms;
   int* d_inj_ptr = nullptr;
   int* d_smp_ptr = nullptr;
   int* d_smp_pts = nullptr;
+  int* d_node_shot = nullptr;  // shot of each injection node (separate injection launches)
   InjNode* d_nodes = nullptr;
   InjTerm* d_terms = nullptr;
   void release() {
     dfree(d_inj_ptr); dfree(d_smp_ptr); dfree(d_smp_pts); dfree(d_nodes); dfree(d_terms);
+    dfree(d_node_shot);
+    d_node_shot = nullptr;
     d_inj_ptr = d_smp_ptr = d_smp_pts = nullptr;
     d_nodes = nullptr;
     d_terms = nullptr;
@@ -739,6 +742,7 @@ static void build_lists(Plan& pl) {
       for (auto& t2 : kv.second) L.terms.push_back(t2);
       nd.tend = (int)L.terms.size();
       L.nodes.push_back(nd);
+      L.node_shot.push_back(pl.units[std::get<0>(kv.first)].shot);
       L.inj_ptr[std::get<0>(kv.first) + 1]++;
     }
     for (int u = 0; u < U; ++u) L.inj_ptr[u + 1] += L.inj_ptr[u];
@@ -752,6 +756,7 @@ static void build_lists(Plan& pl) {
     upload_vec((void**)&L.d_smp_pts, L.smp_pts.data(), L.smp_pts.size() * sizeof(int));
     upload_vec((void**)&L.d_nodes, L.nodes.data(), L.nodes.size() * sizeof(InjNode));
     upload_vec((void**)&L.d_terms, L.terms.data(), L.terms.size() * sizeof(InjTerm));
+    upload_vec((void**)&L.d_node_shot, L.node_shot.data(), L.node_shot.size() * sizeof(int));
   }
   upload_vec((void**)&pl.d_units, pl.units.data(), pl.units.size() * sizeof(Unit));
 }
@@ -936,6 +941,23 @@ static void reset_tickets(Plan& pl, cudaStream_t s) {
   pl.ticket_next = 0;
 }
 
+static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s);
+
+// An adjoint step whose injection (the receiver data: thousands of nodes in a
+// few units) runs as a launch of its own over all SMs after the step, instead
+// of at the tails of the units that hold the nodes.
+static void launch_adjoint_step(Plan& pl, StepArgs a, cudaStream_t s) {
+  const bool inject = (a.flags & kInject) != 0;
+  a.flags &= ~kInject;
+  launch_step(pl, a, s);
+  if (!inject) return;
+  const RoleLists& L = pl.lists[kRoleAdj];
+  const double dt = pl.shots[0]->dt;
+  CK(launch_inject(pl.d_desc[kRoleAdj], L.d_nodes, L.d_node_shot, L.d_terms, (int)L.nodes.size(),
+                   a.inj_row, a.out, a.fslot, (float)(dt * dt), (a.flags & kInjectDiff) != 0,
+                   a.grad, plan_etaf(pl), s));
+}
+
 static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s) {
   const fdw_ctx* c0 = pl.shots[0];
   const bool etaf = plan_etaf(pl);
@@ -1105,7 +1127,7 @@ static void adjoint_body(Plan& pl, cudaStream_t s) {
   if (pl.max_src > 0) flags |= kSample;
   for (int k = nt - 1; k >= 1; --k) {
     StepArgs a{kRoleAdj, (k + 1) & 1, k & 1, k & 1, 0, k, k, flags, false};
-    launch_step(pl, a, s);
+    launch_adjoint_step(pl, a, s);
   }
   if (pl.max_src > 0)
     CK(launch_sample(pl.d_desc[kRoleAdj], (int)pl.shots.size(), pl.max_src, 1, 0, s));
@@ -1137,7 +1159,7 @@ static void gradient_body(Plan& pl, int k, int stype, bool diff, cudaStream_t s)
     // adjoint steps with the imaging condition
     for (int kk = b0 - 1; kk >= std::max(a0, 1); --kk) {
       StepArgs a{kRoleAdj, (kk + 1) & 1, kk & 1, kk & 1, kk - a0 + 1, kk, 0, adj_flags, true};
-      launch_step(pl, a, s);
+      launch_adjoint_step(pl, a, s);
     }
   }
 }
@@ -1204,7 +1226,7 @@ static void revolve_gradient_body(Plan& pl, int k, int stype, bool diff, cudaStr
       }
       for (int kk = b0 - 1; kk >= std::max(a0, 1); --kk) {
         StepArgs a{kRoleAdj, (kk + 1) & 1, kk & 1, kk & 1, slot_of(kk), kk, 0, adj_flags, true};
-        launch_step(pl, a, s);
+        launch_adjoint_step(pl, a, s);
       }
       cur = j;
     }
