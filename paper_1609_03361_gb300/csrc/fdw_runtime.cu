@@ -6,7 +6,12 @@
 // column tile of a shot streamed along an x chunk), per-unit injection and
 // sampling lists for each role (forward, adjoint, recompute) and per-shot
 // descriptors with TMA tensor maps.  Time loops are captured once into CUDA
-// graphs and replayed.
+// graphs and replayed.  Each step launch gets its own unit-ticket counter
+// (CTAs take units in table order as they become free); adjoint steps inject
+// their data in a separate launch.  The gradient pass replays either one
+// checkpoint pair per k steps or a binomial schedule under a memory budget; a
+// context may also be an x slab of a larger grid with ghost planes
+// (single-shot domain decomposition).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
