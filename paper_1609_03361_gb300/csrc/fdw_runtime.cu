@@ -1941,16 +1941,21 @@ fdw_status fdw_step(fdw_ctx* c, int n, const float* q, float* rec, void* stream)
     Plan& pl = ctx_plan(c);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n == 0) CK(cudaMemsetAsync(c->u, 0, sizeof(float) * 2 * c->slot, s));
-    pl.hdesc[kRoleFwd][0].inj_a = q;
-    pl.hdesc[kRoleFwd][0].inj_b = nullptr;
-    pl.hdesc[kRoleFwd][0].smp_out = rec;
-    upload_desc(pl, kRoleFwd, s);
+    ShotDesc& hd = pl.hdesc[kRoleFwd][0];
+    if (n == 0 || hd.inj_a != q || hd.inj_b != nullptr || hd.smp_out != rec) {
+      hd.inj_a = q;
+      hd.inj_b = nullptr;
+      hd.smp_out = rec;
+      upload_desc(pl, kRoleFwd, s);
+    }
     if (n == c->nt - 1) {  // the last time level: samples only
       if (c->rec.n > 0) CK(launch_sample(pl.d_desc[kRoleFwd], 1, c->rec.n, n & 1, n, s));
       c->fwd_done = true;
       return;
     }
-    reset_tickets(pl, s);
+    // one step launch: only its own ticket needs clearing
+    CK(cudaMemsetAsync(pl.d_tickets, 0, sizeof(int), s));
+    pl.ticket_next = 0;
     int flags = 0;
     if (c->src.n > 0) flags |= kInject;
     if (c->rec.n > 0) flags |= kSample;
