@@ -319,12 +319,33 @@ def run_forward(args, world, rank, local):
                "d2h_bytes_per_step": int(rec_h.numel() * 4)}
     s.sync()
 
+    # the adjoint propagator on the same shot (receivers inject the data,
+    # the source samples), graph launched like the forward
+    adjoint = None
+    if not args.no_extras and world == 1:
+        d_dev = rec_dev.clone()
+        s.set_model(m_dev)
+        s.adjoint(d_dev)
+        torch.cuda.synchronize(dev)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(3):
+            s.adjoint(d_dev)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_a = a0.elapsed_time(a1) / 3
+        adjoint = {"workload": "the same shot backwards: 16384 receivers inject, the source samples",
+                   "gpts": updates / (ms_a * 1e-3) / 1e9, "ms_per_run": ms_a}
+        s.sync()
+
     base = None
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
         base = cpu_baseline(w)
 
     extras = {}
     if not args.no_extras and world == 1:   # single-GPU measurements: once, at N = 1
+        extras["adjoint"] = adjoint
         extras["batched"] = run_batched(args.batch_shots, 800, dev)
         extras["fwi"] = run_fwi(args.fwi_shots, args.fwi_nt, 10, dev)
         extras["diffusion"] = run_diffusion(dev)
