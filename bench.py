@@ -702,6 +702,62 @@ def run_so16(args, dev):
     print(json.dumps(line), flush=True)
 
 
+def run_tblock(dev, nt=101, orders=(2, 4)):
+    """Forward on the 256^3 recipe (336^3 computational) at space orders
+    2 and 4: one step per launch (autotuned) against two steps per launch
+    (both row variants), GPts/s, the algorithmic-HBM fraction of each (16 B
+    per point-step for one step; 20 B per point per pass = 10 B per
+    point-step for two) and the traces' difference."""
+    import torch
+    from paper_1609_03361_gb300 import fdwave as fw
+    from paper_1609_03361_gb300 import workloads as W
+    peak, _ = measured_peaks()
+    out = {"workload": f"3D acoustic forward 256^3 (336^3 computational), {nt} steps, FP32",
+           "orders": {}}
+    for p in orders:
+        w = W.config_3d(256, 12.5, p, nt)
+        w.dt = W.choose_dt(fw.fdw_dt_max(3, w.spacing, p, w.vmax))
+        pts = int(np.prod(w.comp_shape))
+        m = torch.from_numpy(w.m.astype(np.float32)).to(dev)
+        q = torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev)
+        res, recs = {}, {}
+        for name, steps, variant in (("one_step", 1, -1), ("two_step_v0", 2, 0),
+                                     ("two_step_v1", 2, 1)):
+            s = fw.Solver(w.shape, w.spacing, p, w.nbl, w.dt, w.nt, w.vmax, device=dev.index or 0)
+            s.set_model(m)
+            s.set_sources(w.src)
+            s.set_receivers(w.rec)
+            if steps == 2:
+                s.set_time_blocking(2, variant)
+            else:
+                s.autotune(10)
+            rec = torch.empty((w.nt, w.rec.shape[0]), device=dev)
+            for _ in range(3):
+                s.forward(q, rec)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            e0.record()
+            for _ in range(reps):
+                s.forward(q, rec)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            s.sync()
+            ms = e0.elapsed_time(e1) / reps
+            g = pts * (w.nt - 1) / (ms * 1e-3) / 1e9
+            b = 16.0 if steps == 1 else 10.0
+            res[name] = {"gpts": g, "ms_per_run": ms, "hbm_frac_alg": g * b / peak,
+                         "config": s.tiling() if steps == 1 else s.time_blocking()}
+            recs[name] = rec.cpu().numpy().astype(np.float64)
+            s.close()
+        ref = recs["one_step"]
+        for name in ("two_step_v0", "two_step_v1"):
+            res[name]["rec_rel_l2_vs_one_step"] = float(
+                np.linalg.norm(recs[name] - ref) / np.linalg.norm(ref))
+        out["orders"][f"so{p}"] = res
+    return out
+
+
 def run_precision(args, dev):
     """Errors of the 16-bit model and snapshot storage.  Model: SO16 with the
     512^3 recipe, traces of FP32 / FP16 / BF16 model storage against the FP64
@@ -790,7 +846,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="forward",
-                    choices=["forward", "so16", "precision", "diffusion", "fwi", "decomp"])
+                    choices=["forward", "so16", "precision", "diffusion", "fwi", "decomp",
+                             "tblock"])
     ap.add_argument("--nt", type=int, default=1000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -818,6 +875,8 @@ def main():
                 print(json.dumps(run_diffusion(dev)), flush=True)
             elif args.workload == "decomp":
                 print(json.dumps(run_decomp(dev)), flush=True)
+            elif args.workload == "tblock":
+                print(json.dumps(run_tblock(dev)), flush=True)
             elif args.workload == "fwi":
                 print(json.dumps(run_fwi(args.fwi_shots, args.fwi_nt, 10, dev)), flush=True)
             else:

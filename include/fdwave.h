@@ -224,6 +224,32 @@ fdw_status fdw_set_tiling(fdw_ctx* ctx, int tile, int xchunk, int stages);
  * out[2] = pipeline stages, out[3] = CTAs per launch, out[4] = work units. */
 fdw_status fdw_get_tiling(fdw_ctx* ctx, int* out5);
 
+/* Temporal blocking of plain forward modelling (fdw_forward, and
+ * fdw_batch_forward when every context of the batch asks for it): with
+ * steps_per_pass = 2 each launch advances the scheme of Sec. 5 (Eq. 3) by two
+ * time steps, u^{n+1} and u^{n+2} from u^{n-1} and u^n, reading the two old
+ * fields and the model once and writing the two new ones (the first step is
+ * recomputed on a halo of r rows / planes around each tile and kept in shared
+ * memory).  Sources and receivers are handled as in the one-step loop and the
+ * traces agree with it to rounding.  The paper has no counterpart: it is a
+ * memory-traffic optimisation of the same scheme.  Only 3D grids, space orders
+ * 2 and 4 and the built-in damping profiles: FDW_ERR_ARG for a 2D grid,
+ * FDW_ERR_ORDER above order 4, FDW_ERR_STATE on a slab context; a damping
+ * field set with fdw_set_damping makes fdw_forward run one step per launch.
+ * The context then holds four wavefield buffers instead of two (allocated
+ * here; FDW_ERR_OOM if that fails).  Checkpointed forward runs, the adjoint
+ * and the gradient always step one step per launch.  variant: 0 (output tiles
+ * of 16 rows at order 2, 12 at order 4, two CTAs per SM) or 1 (32 / 28 rows,
+ * one CTA per SM), -1 = default 0; xchunk: x planes per work unit (0 =
+ * default); stages: pipeline depth (>= 2r + 1, 0 = default).  steps_per_pass =
+ * 1 restores one step per launch. */
+fdw_status fdw_set_time_blocking(fdw_ctx* ctx, int steps_per_pass, int variant, int xchunk,
+                                 int stages);
+
+/* out[0] = steps per pass; with 2: out[1] = variant, out[2] = x-chunk length,
+ * out[3] = pipeline stages, out[4] = work units (needs the model set). */
+fdw_status fdw_get_time_blocking(fdw_ctx* ctx, int* out5);
+
 /* -------------------------------------------------------------- batched shots */
 
 /* Group contexts that share order, spacing, dt, nt and model storage type so

@@ -36,6 +36,9 @@ const void* step_kernel_r5(int tile, bool grad);
 const void* step_kernel_r6(int tile, bool grad);
 const void* step_kernel_r7(int tile, bool grad);
 const void* step_kernel_r8(int tile, bool grad);
+// Two-step (temporally blocked) forward kernel of radius r = 1 .. kTbMaxR and
+// row variant 0 / 1 (fdw_tb.cu); null for other radii.
+const void* tb_kernel_fn(int r, int variant);
 
 // Geometry of one pitched field for the auxiliary kernels.
 struct Geom {

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "fdw_internal.h"
+#include "fdw_tb.h"
 #include "fdwave.h"
 
 namespace fdw {
@@ -224,7 +225,11 @@ struct fdw_ctx {
   double vmax = 1.0;
   long long slot = 0;           // floats per pitched field
 
-  float* u = nullptr;           // 2 slots
+  float* u = nullptr;           // uslots slots (4 with two steps per pass)
+  int uslots = 2;
+  // forward passes of two time steps (fdw_set_time_blocking) and their tiling
+  int tblock = 1;
+  int tb_variant = -1, tb_lx = 0, tb_stages = 0;
   void* m = nullptr;
   int mtype = kF32;
   bool model_set = false;
@@ -326,6 +331,39 @@ struct Plan {
   long long max_points = 0;
   long long max_slot = 0;            // floats per pitched field, largest shot
   int grad_stages = 0, grad_stages_tile = -1;  // pipeline depth of the gradient step
+  // two-step forward passes: their own units (output tiles of TY x 56 points),
+  // injection and sampling lists, shot descriptors and launch shape
+  struct Tb {
+    bool built = false;
+    int variant = 0, lx = 0, stages = 0;
+    std::vector<Unit> units;
+    std::vector<TbShot> hshots;
+    Unit* d_units = nullptr;
+    TbShot* d_shots = nullptr;
+    int* d_inj_ptr = nullptr;
+    int* d_ext_ptr = nullptr;
+    int* d_smp_ptr = nullptr;
+    int* d_smp_pts = nullptr;
+    InjNode* d_inj_nodes = nullptr;
+    InjNode* d_ext_nodes = nullptr;
+    InjTerm* d_inj_terms = nullptr;
+    InjTerm* d_ext_terms = nullptr;
+    const void* fn = nullptr;
+    int grid = 0, threads = 0, stage_bytes = 0, off_p = 0, off_s = 0;
+    size_t smem = 0;
+    void release() {
+      dfree(d_units); dfree(d_shots); dfree(d_inj_ptr); dfree(d_ext_ptr); dfree(d_smp_ptr);
+      dfree(d_smp_pts); dfree(d_inj_nodes); dfree(d_ext_nodes); dfree(d_inj_terms);
+      dfree(d_ext_terms);
+      d_units = nullptr; d_shots = nullptr;
+      d_inj_ptr = d_ext_ptr = d_smp_ptr = d_smp_pts = nullptr;
+      d_inj_nodes = d_ext_nodes = nullptr;
+      d_inj_terms = d_ext_terms = nullptr;
+      units.clear();
+      hshots.clear();
+      built = false;
+    }
+  } tb;
   // one unit-ticket counter per step launch of a pass, zeroed at the pass start
   int* d_tickets = nullptr;
   int ticket_cap = 0, ticket_next = 0;
@@ -348,6 +386,7 @@ struct Plan {
     dfree(d_pack);
     dfree(d_unpack);
     dfree(d_rv);
+    tb.release();
     if (cap) cudaStreamDestroy(cap);
   }
 };
@@ -774,8 +813,10 @@ static ShotDesc make_desc(const Plan& pl, fdw_ctx* c, int role) {
   const int R4 = (pl.r + 3) & ~3;
   float* ubuf = nullptr;
   int uslots = 2;
-  if (role == kRoleFwd) ubuf = c->u;
-  else if (role == kRoleAdj) ubuf = c->lam;
+  if (role == kRoleFwd) {
+    ubuf = c->u;
+    uslots = c->uslots;
+  } else if (role == kRoleAdj) ubuf = c->lam;
   else { ubuf = c->seg; uslots = c->seg_slots; }
   d.nx = c->nx; d.ny = c->ny; d.nz = c->nz; d.nzp = c->nzp;
   d.mtype = c->mtype;
@@ -826,6 +867,7 @@ static std::vector<int> current_versions(const Plan& pl) {
     v.push_back(c->buffers_version);
     v.push_back(c->mtype);
     v.push_back(c->use_etaf ? 1 : 0);
+    v.push_back(c->tblock);
   }
   return v;
 }
@@ -857,6 +899,7 @@ static void ensure_plan(Plan& pl) {
   if (pl.built && v == pl.built_versions) return;
   if (!pl.built) choose_default_tiling(pl);
   build_lists(pl);
+  pl.tb.release();
   for (int role = 0; role < kNumRoles; ++role) {
     pl.hdesc[role].clear();
     for (auto* c : pl.shots) pl.hdesc[role].push_back(make_desc(pl, c, role));
@@ -963,12 +1006,28 @@ static void launch_adjoint_step(Plan& pl, StepArgs a, cudaStream_t s) {
                    a.grad, plan_etaf(pl), s));
 }
 
-static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s) {
+// dt^2 c_k / h_a^2 per axis (k = 1..r; an inactive axis of a 2D grid gets
+// zeros), the sum of the centre weights over the axes, and dt^2.
+static void stencil_weights(Plan& pl, float w[3][kMaxR + 1], float* csum, float* dt2) {
   const fdw_ctx* c0 = pl.shots[0];
+  if (pl.weights.empty()) pl.weights = fornberg_second_derivative(c0->order);
+  const double dt = c0->dt;
+  *dt2 = (float)(dt * dt);
+  const std::vector<double>& cw = pl.weights;
+  double cs = 0.0;
+  for (int ax = 0; ax < 3; ++ax) {
+    const bool active = !(c0->ny == 1 && c0->ndim == 2 && ax == 1);
+    const double sc = active ? dt * dt / (c0->h[ax] * c0->h[ax]) : 0.0;
+    for (int k = 0; k <= kMaxR; ++k) w[ax][k] = (k <= pl.r) ? (float)(cw[k] * sc) : 0.f;
+    cs += cw[0] * sc;
+  }
+  *csum = (float)cs;
+}
+
+static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s) {
   const bool etaf = plan_etaf(pl);
   const Plan::LaunchInfo& li = launch_info(pl, a.grad);
   const int nunits = (int)pl.units.size();
-  if (pl.weights.empty()) pl.weights = fornberg_second_derivative(c0->order);
 
   StepParams P;
   std::memset(&P, 0, sizeof(P));
@@ -1000,17 +1059,7 @@ static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s) {
   P.off_f = li.off_f;
   P.off_a = li.off_a;
   P.off_e = li.off_e;
-  const double dt = c0->dt;
-  P.dt2 = (float)(dt * dt);
-  const std::vector<double>& cw = pl.weights;
-  double csum = 0.0;
-  for (int ax = 0; ax < 3; ++ax) {
-    const bool active = !(c0->ny == 1 && c0->ndim == 2 && ax == 1);
-    const double sc = active ? dt * dt / (c0->h[ax] * c0->h[ax]) : 0.0;
-    for (int k = 0; k <= kMaxR; ++k) P.w[ax][k] = (k <= pl.r) ? (float)(cw[k] * sc) : 0.f;
-    csum += cw[0] * sc;
-  }
-  P.csum = (float)csum;
+  stencil_weights(pl, P.w, &P.csum, &P.dt2);
   P.err = pl.d_err;
 
   cudaLaunchConfig_t cfg;
@@ -1121,6 +1170,318 @@ static void forward_body(Plan& pl, int k, int stype, cudaStream_t s) {
   }
   if (pl.max_rec > 0)
     CK(launch_sample(pl.d_desc[kRoleFwd], (int)pl.shots.size(), pl.max_rec, (nt - 1) & 1, nt - 1, s));
+}
+
+// ---------------------------------------------------------------- two steps per pass
+
+// A plan runs its plain forward passes two steps per launch when every shot
+// asks for it (fdw_set_time_blocking) and takes its damping from the profiles.
+static bool plan_uses_tb(const Plan& pl) {
+  for (auto* c : pl.shots)
+    if (c->tblock != 2 || c->use_etaf) return false;
+  return true;
+}
+
+struct TbLayout {
+  int bytes, off_p, off_s;
+  size_t smem;
+};
+
+// Stage of the two-step kernel: the halo box of u^n, then the region-E tiles
+// of u^{n-1} and s; after the stages, 2r + 2 region-E planes of u^{n+1}.
+static TbLayout tb_layout(int r, int variant, int mtype, int stages) {
+  const int EY = tb_ey(r, variant), HY = EY + 2 * r;
+  TbLayout L;
+  L.off_p = round128(HY * kTbHZ * 4);
+  L.off_s = L.off_p + round128(EY * kTbEZ * 4);
+  L.bytes = L.off_s + round128(mtype == kF32 ? EY * kTbEZ * 4 : EY * kTbHZ * 2);
+  L.smem = (size_t)stages * L.bytes + (size_t)(2 * r + 2) * EY * kTbEZ * 4 +
+           (size_t)(2 * stages) * 8 + 128;
+  return L;
+}
+
+// Units, lists, descriptors and launch shape of the two-step kernel.
+static void build_tb(Plan& pl) {
+  Plan::Tb& T = pl.tb;
+  T.release();
+  const int r = pl.r;
+  const fdw_ctx* c0 = pl.shots[0];
+  T.variant = c0->tb_variant >= 0 ? c0->tb_variant : 0;
+  const int EY = tb_ey(r, T.variant), TY = tb_ty(r, T.variant);
+  const int mt = plan_mtype(pl);
+  T.fn = tb_kernel_fn(r, T.variant);
+  if (!T.fn) fail(FDW_ERR_ORDER, "no two-step kernel for this space order");
+  // by default the deepest pipeline that keeps the CTAs per SM the registers
+  // allow (two of variant 0, one of variant 1): the 2r + 1 planes held (a
+  // plane's stage serves the first step at x and the second step r planes
+  // later) and as many in flight as fit
+  int smem_sm = 0;
+  CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, pl.device));
+  const size_t cap = (size_t)device_smem_optin(pl.device) - 1024;
+  const size_t cap_cta = std::min(cap, (size_t)smem_sm / (T.variant == 0 ? 2 : 1) - 2048);
+  int st = std::min(c0->tb_stages > 0 ? c0->tb_stages : kMaxStages, kMaxStages);
+  while (st > 2 * r + 1 &&
+         tb_layout(r, T.variant, mt, st).smem > (c0->tb_stages > 0 ? cap : cap_cta))
+    --st;
+  const TbLayout L = tb_layout(r, T.variant, mt, st);
+  if (L.smem > cap) fail(FDW_ERR_ARG, "two-step pipeline does not fit in shared memory");
+  T.stages = st;
+  T.smem = L.smem;
+  T.stage_bytes = L.bytes;
+  T.off_p = L.off_p;
+  T.off_s = L.off_s;
+  T.threads = EY * 16 + 32;
+  configure_kernel(T.fn, T.smem);
+  int nb = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, T.fn, T.threads, T.smem));
+  const long long slots = (long long)std::max(nb, 1) * device_sms(pl.device);
+
+  // rows of units (an x chunk of one shot times its column tiles), the last
+  // resident round cut into quarters as for the one-step kernel
+  const size_t ns = pl.shots.size();
+  std::vector<std::array<int, 2>> cols(ns);
+  long long ncols = 0;
+  int nxmax = 1;
+  for (size_t s = 0; s < ns; ++s) {
+    const fdw_ctx* c = pl.shots[s];
+    cols[s] = {(c->ny + TY - 1) / TY, (c->nz + kTbTZ - 1) / kTbTZ};
+    ncols += (long long)cols[s][0] * cols[s][1];
+    nxmax = std::max(nxmax, c->nx);
+  }
+  int lx = c0->tb_lx;
+  if (lx <= 0) {  // the longest chunk (nx / 2^k) that gives two units per resident CTA
+    lx = nxmax;
+    while (lx > 8 * r && ncols * ((nxmax + lx - 1) / lx) < 2 * slots) lx = (lx + 1) / 2;
+  }
+  T.lx = lx;
+  struct Row {
+    int shot, x0, x1;
+    bool split;
+  };
+  std::vector<Row> rows;
+  for (size_t s = 0; s < ns; ++s)
+    for (int x0 = 0; x0 < pl.shots[s]->nx; x0 += lx)
+      rows.push_back(Row{(int)s, x0, std::min(pl.shots[s]->nx, x0 + lx), false});
+  {
+    long long covered = 0;
+    for (size_t i = rows.size(); i-- > 0 && covered < slots;) {
+      covered += (long long)cols[rows[i].shot][0] * cols[rows[i].shot][1];
+      rows[i].split = true;
+    }
+  }
+  std::vector<Row> fine;
+  for (const Row& rw : rows) {
+    const int len = rw.x1 - rw.x0, piece = std::max(8, (len + 3) / 4);
+    if (!rw.split || len <= piece) {
+      fine.push_back(rw);
+      continue;
+    }
+    for (int x0 = rw.x0; x0 < rw.x1; x0 += piece)
+      fine.push_back(Row{rw.shot, x0, std::min(rw.x1, x0 + piece), true});
+  }
+  std::vector<int> rbase(fine.size());
+  std::vector<std::vector<int>> xrow(ns);
+  for (size_t s = 0; s < ns; ++s) xrow[s].assign(pl.shots[s]->nx, -1);
+  for (size_t ri = 0; ri < fine.size(); ++ri) {
+    const Row& rw = fine[ri];
+    rbase[ri] = (int)T.units.size();
+    for (int x = rw.x0; x < rw.x1; ++x) xrow[rw.shot][x] = (int)ri;
+    for (int jy = 0; jy < cols[rw.shot][0]; ++jy)
+      for (int jz = 0; jz < cols[rw.shot][1]; ++jz) {
+        Unit un{};
+        un.shot = rw.shot;
+        un.x0 = rw.x0;
+        un.x1 = rw.x1;
+        un.y0 = jy * TY;
+        un.z0 = jz * kTbTZ;
+        T.units.push_back(un);
+      }
+  }
+  const int U = (int)T.units.size();
+  auto unit_at = [&](int ri, int jy, int jz) {
+    return rbase[ri] + jy * cols[fine[ri].shot][1] + jz;
+  };
+
+  // source nodes: owned (unit of the node) and seen (units whose region E
+  // over their first-step planes holds the node); std::map keeps each unit's
+  // nodes in (x, y, z) order
+  std::map<std::tuple<int, int, int, int>, std::vector<InjTerm>> own, ext;
+  std::vector<std::vector<int>> smp(U);
+  for (size_t s = 0; s < ns; ++s) {
+    const fdw_ctx* c = pl.shots[s];
+    for (int j = 0; j < c->src.n; ++j)
+      for (int cc = 0; cc < 8; ++cc) {
+        const float w = c->src.w[(size_t)j * 8 + cc];
+        if (w == 0.f) continue;
+        const int x = c->src.base[(size_t)j * 3] + ((cc >> 2) & 1);
+        const int y = c->src.base[(size_t)j * 3 + 1] + ((cc >> 1) & 1);
+        const int z = c->src.base[(size_t)j * 3 + 2] + (cc & 1);
+        own[std::make_tuple(unit_at(xrow[s][x], y / TY, z / kTbTZ), x, y, z)].push_back(
+            InjTerm{j, w});
+        int last_ri = -1;
+        for (int xx = std::max(0, x - r); xx <= std::min(c->nx - 1, x + r); ++xx) {
+          const int ri = xrow[s][xx];
+          if (ri == last_ri) continue;
+          last_ri = ri;
+          const Row& rw = fine[ri];
+          if (x < rw.x0 - r || x >= rw.x1 + r) continue;
+          for (int jy = 0; jy < cols[s][0]; ++jy) {
+            if (y < jy * TY - r || y >= jy * TY + TY + r) continue;
+            for (int jz = 0; jz < cols[s][1]; ++jz) {
+              if (z < jz * kTbTZ - 4 || z >= jz * kTbTZ + kTbTZ + 4) continue;
+              ext[std::make_tuple(unit_at(ri, jy, jz), x, y, z)].push_back(InjTerm{j, w});
+            }
+          }
+        }
+      }
+    for (int j = 0; j < c->rec.n; ++j) {
+      const int* b = &c->rec.base[(size_t)j * 3];
+      smp[unit_at(xrow[s][b[0]], b[1] / TY, b[2] / kTbTZ)].push_back(j);
+    }
+  }
+  auto flatten = [&](const std::map<std::tuple<int, int, int, int>, std::vector<InjTerm>>& m,
+                     std::vector<int>& ptr, std::vector<InjNode>& nodes,
+                     std::vector<InjTerm>& terms) {
+    ptr.assign(U + 1, 0);
+    for (auto& kv : m) {
+      InjNode nd{};
+      nd.x = std::get<1>(kv.first);
+      nd.y = std::get<2>(kv.first);
+      nd.z = std::get<3>(kv.first);
+      nd.tbeg = (int)terms.size();
+      for (const InjTerm& t : kv.second) terms.push_back(t);
+      nd.tend = (int)terms.size();
+      nodes.push_back(nd);
+      ptr[std::get<0>(kv.first) + 1]++;
+    }
+    for (int u = 0; u < U; ++u) ptr[u + 1] += ptr[u];
+  };
+  std::vector<int> inj_ptr, ext_ptr, smp_ptr(U + 1, 0), smp_pts;
+  std::vector<InjNode> inj_nodes, ext_nodes;
+  std::vector<InjTerm> inj_terms, ext_terms;
+  flatten(own, inj_ptr, inj_nodes, inj_terms);
+  flatten(ext, ext_ptr, ext_nodes, ext_terms);
+  for (int u = 0; u < U; ++u) {
+    smp_ptr[u + 1] = smp_ptr[u] + (int)smp[u].size();
+    for (int j : smp[u]) smp_pts.push_back(j);
+  }
+  upload_vec((void**)&T.d_units, T.units.data(), T.units.size() * sizeof(Unit));
+  upload_vec((void**)&T.d_inj_ptr, inj_ptr.data(), inj_ptr.size() * sizeof(int));
+  upload_vec((void**)&T.d_ext_ptr, ext_ptr.data(), ext_ptr.size() * sizeof(int));
+  upload_vec((void**)&T.d_smp_ptr, smp_ptr.data(), smp_ptr.size() * sizeof(int));
+  upload_vec((void**)&T.d_smp_pts, smp_pts.data(), smp_pts.size() * sizeof(int));
+  upload_vec((void**)&T.d_inj_nodes, inj_nodes.data(), inj_nodes.size() * sizeof(InjNode));
+  upload_vec((void**)&T.d_ext_nodes, ext_nodes.data(), ext_nodes.size() * sizeof(InjNode));
+  upload_vec((void**)&T.d_inj_terms, inj_terms.data(), inj_terms.size() * sizeof(InjTerm));
+  upload_vec((void**)&T.d_ext_terms, ext_terms.data(), ext_terms.size() * sizeof(InjTerm));
+
+  const CUtensorMapDataType mdt = mt == kF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                  : mt == kBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  for (auto* c : pl.shots) {
+    TbShot d;
+    std::memset(&d, 0, sizeof(d));
+    make_map(&d.tm_uh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->u, c->nx, c->ny, c->nz, c->nzp, 4,
+             c->slot, kTbHZ, EY + 2 * r);
+    make_map(&d.tm_ue, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->u, c->nx, c->ny, c->nz, c->nzp, 4,
+             c->slot, kTbEZ, EY);
+    make_map(&d.tm_s, mdt, msize(mt), c->m, c->nx, c->ny, c->nz, c->nzp, 0, c->slot,
+             mt == kF32 ? kTbEZ : kTbHZ, EY);
+    d.u = c->u;
+    d.uslot = c->slot;
+    d.m = c->m;
+    d.eta = c->eta;
+    d.nx = c->nx;
+    d.ny = c->ny;
+    d.nz = c->nz;
+    d.nzp = c->nzp;
+    d.mtype = mt;
+    d.q_ld = c->src.n;
+    d.rec_ld = c->rec.n;
+    d.pt_base = c->rec.d_base;
+    d.pt_w = c->rec.d_w;
+    T.hshots.push_back(d);
+  }
+  T.d_shots = dalloc<TbShot>(ns);
+  T.grid = (int)std::max(1LL, std::min<long long>(U, slots));
+  T.built = true;
+}
+
+// One two-step launch: u^{n+1}, u^{n+2} from u^{n-1}, u^n (u^t in slot t mod
+// 4), wavelet rows n and n + 1 injected, trace rows srow_prev (-1: none) and
+// n sampled from u^{n-1} and u^n.
+static void launch_tb(Plan& pl, int n, int srow_prev, int flags, cudaStream_t s) {
+  const Plan::Tb& T = pl.tb;
+  TbParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.shots = T.d_shots;
+  P.units = T.d_units;
+  P.nunits = (int)T.units.size();
+  if (pl.ticket_next >= pl.ticket_cap) fail(FDW_ERR_ARG, "too many step launches in one pass");
+  P.ticket = pl.d_tickets + pl.ticket_next++;
+  P.flags = flags;
+  P.inj_ptr = T.d_inj_ptr;
+  P.inj_nodes = T.d_inj_nodes;
+  P.inj_terms = T.d_inj_terms;
+  P.ext_ptr = T.d_ext_ptr;
+  P.ext_nodes = T.d_ext_nodes;
+  P.ext_terms = T.d_ext_terms;
+  P.smp_ptr = T.d_smp_ptr;
+  P.smp_pts = T.d_smp_pts;
+  P.row1 = n;
+  P.row2 = n + 1;
+  P.srow_prev = srow_prev;
+  P.srow_cur = n;
+  P.prev = (n + 3) & 3;
+  P.cur = n & 3;
+  P.out1 = (n + 1) & 3;
+  P.out2 = (n + 2) & 3;
+  P.stages = T.stages;
+  P.stage_bytes = T.stage_bytes;
+  P.off_p = T.off_p;
+  P.off_s = T.off_s;
+  stencil_weights(pl, P.w, &P.csum, &P.dt2);
+  P.err = pl.d_err;
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(T.grid);
+  cfg.blockDim = dim3(T.threads);
+  cfg.dynamicSmemBytes = T.smem;
+  cfg.stream = s;
+  void* args[] = {&P};
+  CK(cudaLaunchKernelExC(&cfg, T.fn, args));
+}
+
+// Plain forward loop, two steps per launch.  An odd number of steps starts
+// with one one-step launch; the last two time levels are sampled by the
+// sampling kernel and copied to the slots the one-step loop leaves them in
+// (u^t in slot t & 1).
+static void tb_forward_body(Plan& pl, cudaStream_t s) {
+  const int nt = pl.shots[0]->nt;
+  reset_tickets(pl, s);
+  for (auto* c : pl.shots) CK(cudaMemsetAsync(c->u, 0, sizeof(float) * 4 * c->slot, s));
+  int flags = 0;
+  if (pl.max_src > 0) flags |= kInject;
+  if (pl.max_rec > 0) flags |= kSample;
+  int n = 0, next_row = 0;  // next_row: first trace row not yet recorded
+  if ((nt - 1) % 2 == 1) {
+    StepArgs a{kRoleFwd, 0, 3, 1, 0, 0, 0, flags, false};
+    launch_step(pl, a, s);
+    n = 1;
+    next_row = 1;
+  }
+  for (; n + 2 < nt; n += 2) {
+    launch_tb(pl, n, n - 1 >= next_row ? n - 1 : -1, flags, s);
+    next_row = n + 1;
+  }
+  if (pl.max_rec > 0)
+    for (int row = next_row; row < nt; ++row)
+      CK(launch_sample(pl.d_desc[kRoleFwd], (int)pl.shots.size(), pl.max_rec, row & 3, row, s));
+  for (int t = std::max(0, nt - 2); t < nt; ++t)
+    if ((t & 3) != (t & 1))
+      for (auto* c : pl.shots)
+        CK(cudaMemcpyAsync(c->u + (size_t)(t & 1) * c->slot, c->u + (size_t)(t & 3) * c->slot,
+                           sizeof(float) * c->slot, cudaMemcpyDeviceToDevice, s));
 }
 
 static void adjoint_body(Plan& pl, cudaStream_t s) {
@@ -1402,6 +1763,8 @@ static void plan_forward(Plan& pl, const float* const* q, float* const* rec, int
                          cudaStream_t s) {
   const size_t ns = pl.shots.size();
   pl.test_stall = env_flag("FDW_TEST_STALL") && env_flag("FDW_NO_GRAPH");
+  const bool tb = k == 0 && plan_uses_tb(pl);
+  if (tb && !pl.tb.built) build_tb(pl);
   std::vector<std::pair<float*, float*>> copies;  // (host dst, staging src)
   std::vector<size_t> sizes;
   for (size_t i = 0; i < ns; ++i) {
@@ -1419,9 +1782,16 @@ static void plan_forward(Plan& pl, const float* const* q, float* const* rec, int
     pl.hdesc[kRoleFwd][i].inj_a = qd;
     pl.hdesc[kRoleFwd][i].inj_b = nullptr;
     pl.hdesc[kRoleFwd][i].smp_out = rd;
+    if (tb) {
+      pl.tb.hshots[i].q = qd;
+      pl.tb.hshots[i].rec = rd;
+    }
     if (k > 0 && nq > 0) CK(cudaMemcpyAsync(c->qsave, qd, nq * sizeof(float), cudaMemcpyDeviceToDevice, s));
   }
   upload_desc(pl, kRoleFwd, s);
+  if (tb)
+    CK(cudaMemcpyAsync(pl.tb.d_shots, pl.tb.hshots.data(), sizeof(TbShot) * ns,
+                       cudaMemcpyHostToDevice, s));
   if (k > 0) {
     ensure_aux(pl);
     for (size_t i = 0; i < ns; ++i) pl.hdesc[kRoleRec][i].inj_a = pl.shots[i]->qsave;
@@ -1429,7 +1799,11 @@ static void plan_forward(Plan& pl, const float* const* q, float* const* rec, int
   }
   std::ostringstream key;
   key << "fwd k" << k << " t" << stype << " rv" << (k > 0 && pl.shots[0]->revolve ? pl.shots[0]->nsnap : 0);
-  run_graph(pl, key.str(), s, [&](cudaStream_t st) { forward_body(pl, k, stype, st); });
+  if (tb) key << " tb";
+  run_graph(pl, key.str(), s, [&](cudaStream_t st) {
+    if (tb) tb_forward_body(pl, st);
+    else forward_body(pl, k, stype, st);
+  });
   for (size_t i = 0; i < copies.size(); ++i)
     CK(cudaMemcpyAsync(copies[i].first, copies[i].second, sizes[i] * sizeof(float),
                        cudaMemcpyDeviceToHost, s));
@@ -2101,6 +2475,57 @@ fdw_status fdw_get_tiling(fdw_ctx* c, int* out5) {
     out5[2] = pl.stages;
     out5[3] = std::min((int)pl.units.size(), resident_ctas(pl, pl.tile, pl.stages, false));
     out5[4] = (int)pl.units.size();
+  });
+}
+
+fdw_status fdw_set_time_blocking(fdw_ctx* c, int steps, int variant, int xchunk, int stages) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    if (steps != 1 && steps != 2) fail(FDW_ERR_ARG, "steps per pass must be 1 or 2");
+    if (variant < -1 || variant >= kTbVariants || xchunk < 0 || stages < 0)
+      fail(FDW_ERR_ARG, "bad two-step tiling");
+    if (steps == 2) {
+      if (c->ndim != 3) fail(FDW_ERR_ARG, "two steps per pass need a 3D grid");
+      if (c->r > kTbMaxR) fail(FDW_ERR_ORDER, "two steps per pass exist for space orders 2 and 4");
+      if (c->slab) fail(FDW_ERR_STATE, "a slab context steps one step at a time (fdw_step)");
+      if (stages > 0 && stages < 2 * c->r + 1) fail(FDW_ERR_ARG, "stages must be >= 2r + 1");
+      if (c->uslots < 4) {  // u^t lives in slot t mod 4 during a two-step pass
+        set_device(c->device);
+        CK(cudaDeviceSynchronize());
+        float* nu = dalloc<float>((size_t)c->slot * 4);
+        CK(cudaMemset(nu, 0, sizeof(float) * 4 * c->slot));
+        dfree(c->u);
+        c->u = nu;
+        c->uslots = 4;
+        c->fwd_done = false;
+        c->buffers_version++;
+      }
+    }
+    c->tblock = steps;
+    c->tb_variant = variant;
+    c->tb_lx = xchunk;
+    c->tb_stages = stages;
+    if (c->plan) {
+      c->plan->tb.release();
+      c->plan->clear_graphs();
+    }
+  });
+}
+
+fdw_status fdw_get_time_blocking(fdw_ctx* c, int* out5) {
+  if (!c || !out5) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    for (int i = 0; i < 5; ++i) out5[i] = 0;
+    out5[0] = c->tblock;
+    if (c->tblock != 2) return;
+    require_model(c);
+    set_device(c->device);
+    Plan& pl = ctx_plan(c);
+    if (!pl.tb.built) build_tb(pl);
+    out5[1] = pl.tb.variant;
+    out5[2] = pl.tb.lx;
+    out5[3] = pl.tb.stages;
+    out5[4] = (int)pl.tb.units.size();
   });
 }
 

@@ -69,6 +69,8 @@ _SIGS = [
     ("fdw_autotune", _I, [_P, _I]),
     ("fdw_set_tiling", _I, [_P, _I, _I, _I]),
     ("fdw_get_tiling", _I, [_P, ctypes.POINTER(_I)]),
+    ("fdw_set_time_blocking", _I, [_P, _I, _I, _I, _I]),
+    ("fdw_get_time_blocking", _I, [_P, ctypes.POINTER(_I)]),
     ("fdw_batch_create", _I, [ctypes.POINTER(_P), _I, _PP]),
     ("fdw_batch_destroy", None, [_P]),
     ("fdw_batch_last_error", ctypes.c_char_p, [_P]),
@@ -304,6 +306,17 @@ def fdw_set_tiling(ctx, tile=-1, xchunk=0, stages=0):
     _check(lib().fdw_set_tiling(ctx, int(tile), int(xchunk), int(stages)), ctx)
 
 
+def fdw_set_time_blocking(ctx, steps_per_pass, variant=-1, xchunk=0, stages=0):
+    _check(lib().fdw_set_time_blocking(ctx, int(steps_per_pass), int(variant), int(xchunk),
+                                       int(stages)), ctx)
+
+
+def fdw_get_time_blocking(ctx):
+    out = (ctypes.c_int * 5)()
+    _check(lib().fdw_get_time_blocking(ctx, out), ctx)
+    return dict(zip(("steps", "variant", "xchunk", "stages", "units"), list(out)))
+
+
 def fdw_set_checkpoint_budget(ctx, max_pairs):
     _check(lib().fdw_set_checkpoint_budget(ctx, int(max_pairs)), ctx)
 
@@ -530,6 +543,13 @@ class Solver:
 
     def tiling(self):
         return fdw_get_tiling(self.ctx)
+
+    def set_time_blocking(self, steps_per_pass, variant=-1, xchunk=0, stages=0):
+        """Plain forward runs advance two time steps per launch (steps_per_pass=2)."""
+        fdw_set_time_blocking(self.ctx, steps_per_pass, variant, xchunk, stages)
+
+    def time_blocking(self):
+        return fdw_get_time_blocking(self.ctx)
 
 
 class Batch:
