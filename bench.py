@@ -8,7 +8,7 @@ FP32 arithmetic, FP32 model.  Inputs are synthetic (seeded two-layer model with
 a smoothed +-5% perturbation).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload forward|fwi|batched]
+                    [--workload forward|so16|precision|diffusion|fwi|decomp|tblock]
 
 Prints one JSON line (rank 0).  `value` is device-timed throughput in grid-point
 updates per second (GPts/s) with inputs resident in HBM; `e2e` is the same
@@ -350,6 +350,7 @@ def run_forward(args, world, rank, local):
         extras["fwi"] = run_fwi(args.fwi_shots, args.fwi_nt, 10, dev)
         extras["diffusion"] = run_diffusion(dev)
         extras["decomposition"] = run_decomp(dev)
+        extras["two_step"] = run_tblock(dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GPts/s", "n_gpus": world,
@@ -702,7 +703,7 @@ def run_so16(args, dev):
     print(json.dumps(line), flush=True)
 
 
-def run_tblock(dev, nt=101, orders=(2, 4)):
+def run_tblock(dev, nt=101, orders=(2, 4), variants=(0, 1), baseline=True, reps=5):
     """Forward on the 256^3 recipe (336^3 computational) at space orders
     2 and 4: one step per launch (autotuned) against two steps per launch
     (both row variants), GPts/s, the algorithmic-HBM fraction of each (16 B
@@ -721,8 +722,9 @@ def run_tblock(dev, nt=101, orders=(2, 4)):
         m = torch.from_numpy(w.m.astype(np.float32)).to(dev)
         q = torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev)
         res, recs = {}, {}
-        for name, steps, variant in (("one_step", 1, -1), ("two_step_v0", 2, 0),
-                                     ("two_step_v1", 2, 1)):
+        runs = ([("one_step", 1, -1)] if baseline else []) + \
+            [(f"two_step_v{v}", 2, v) for v in variants]
+        for name, steps, variant in runs:
             s = fw.Solver(w.shape, w.spacing, p, w.nbl, w.dt, w.nt, w.vmax, device=dev.index or 0)
             s.set_model(m)
             s.set_sources(w.src)
@@ -736,7 +738,6 @@ def run_tblock(dev, nt=101, orders=(2, 4)):
                 s.forward(q, rec)
             torch.cuda.synchronize(dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 5
             e0.record()
             for _ in range(reps):
                 s.forward(q, rec)
@@ -750,10 +751,12 @@ def run_tblock(dev, nt=101, orders=(2, 4)):
                          "config": s.tiling() if steps == 1 else s.time_blocking()}
             recs[name] = rec.cpu().numpy().astype(np.float64)
             s.close()
-        ref = recs["one_step"]
-        for name in ("two_step_v0", "two_step_v1"):
-            res[name]["rec_rel_l2_vs_one_step"] = float(
-                np.linalg.norm(recs[name] - ref) / np.linalg.norm(ref))
+        if baseline:
+            ref = recs["one_step"]
+            for name in recs:
+                if name != "one_step":
+                    res[name]["rec_rel_l2_vs_one_step"] = float(
+                        np.linalg.norm(recs[name] - ref) / np.linalg.norm(ref))
         out["orders"][f"so{p}"] = res
     return out
 
@@ -857,6 +860,11 @@ def main():
     ap.add_argument("--batch-shots", type=int, default=64)
     ap.add_argument("--fwi-shots", type=int, default=16)
     ap.add_argument("--fwi-nt", type=int, default=2000)
+    ap.add_argument("--tb-orders", default="2,4", help="space orders of --workload tblock")
+    ap.add_argument("--tb-variants", default="0,1", help="two-step row variants to time")
+    ap.add_argument("--tb-no-baseline", action="store_true",
+                    help="skip the one-step runs of --workload tblock")
+    ap.add_argument("--tb-reps", type=int, default=5, help="timed runs per tblock config")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
@@ -876,7 +884,11 @@ def main():
             elif args.workload == "decomp":
                 print(json.dumps(run_decomp(dev)), flush=True)
             elif args.workload == "tblock":
-                print(json.dumps(run_tblock(dev)), flush=True)
+                print(json.dumps(run_tblock(
+                    dev, args.nt if args.nt != 1000 else 101,
+                    tuple(int(v) for v in args.tb_orders.split(",")),
+                    tuple(int(v) for v in args.tb_variants.split(",")),
+                    not args.tb_no_baseline, args.tb_reps)), flush=True)
             elif args.workload == "fwi":
                 print(json.dumps(run_fwi(args.fwi_shots, args.fwi_nt, 10, dev)), flush=True)
             else:
