@@ -11,12 +11,14 @@
 //    q of u^n: the halo box of the plane (region E grown by r rows and 4
 //    points, zero-filled outside the grid) and, for the planes of the first
 //    step, the region-E tiles of u^{n-1} and s;
-//  - consumer thread (ry, qz) owns one four-point quad of region E.  At plane
-//    p it computes u^{n+1} there (first step: x neighbours from a register
-//    queue of u^n, y and z neighbours from the halo box), writes it into a
-//    ring of R + 2 region-E planes in shared memory, and, on the output tile,
-//    computes u^{n+2} at plane p - r (second step: x neighbours from a
-//    register queue of u^{n+1}, y and z neighbours from the shared plane);
+//  - first step: consumer thread (ry, qz) owns one four-point quad of region
+//    E; at plane p it computes u^{n+1} there (x neighbours from a register
+//    queue of u^n, y and z neighbours from the halo box) and writes it into a
+//    ring of 2r + 2 region-E planes in shared memory;
+//  - second step, r planes behind: thread (ty, tq) owns one quad of the
+//    output tile and computes u^{n+2} at plane x = p - r with every neighbour
+//    from that ring; u^n and s at x come from plane x's stage, which stays
+//    held until then (the pipeline keeps at least 2r + 1 stages);
 //  - the first step's points outside the grid are set to zero, which is the
 //    scheme's zero halo for the second step;
 //  - sources inside region E are added into the shared u^{n+1} plane before
