@@ -868,6 +868,9 @@ static std::vector<int> current_versions(const Plan& pl) {
     v.push_back(c->mtype);
     v.push_back(c->use_etaf ? 1 : 0);
     v.push_back(c->tblock);
+    v.push_back(c->tb_variant);
+    v.push_back(c->tb_lx);
+    v.push_back(c->tb_stages);
   }
   return v;
 }
