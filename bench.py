@@ -139,11 +139,16 @@ def max_over_ranks(x, world):
 
 # ---------------------------------------------------------------- workloads
 
-def cfg2_workload(nt=1000):
-    from paper_1609_03361_gb300 import fdwave as fw
+def cfg2_workload(nt=1000, dt_max=None):
+    """The 256^3 SO8 workload; `dt_max(ndim, spacing, order, vmax)` gives the
+    stability limit (the library's by default; the oracle arm passes the
+    oracle's own, so it never loads the library)."""
     from paper_1609_03361_gb300 import workloads as W
+    if dt_max is None:
+        from paper_1609_03361_gb300 import fdwave as fw
+        dt_max = fw.fdw_dt_max
     w = W.config_3d(256, 12.5, 8, nt)
-    w.dt = W.choose_dt(fw.fdw_dt_max(3, 12.5, 8, w.vmax))
+    w.dt = W.choose_dt(dt_max(3, 12.5, 8, w.vmax))
     return w
 
 
@@ -192,8 +197,8 @@ def cpu_baseline(w, target_s=15.0):
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    w = cfg2_workload()
     import oracle
+    w = cfg2_workload(dt_max=oracle.dt_max)
     pts = int(np.prod(w.comp_shape))
     s2 = oracle.Setup(w.shape, w.spacing, w.space_order, w.nbl, w.dt, 2)
     M = oracle.extend_model(s2, w.m.astype(np.float32).astype(np.float64))
@@ -207,7 +212,7 @@ def run_reference(args, world, rank):
         return time.perf_counter() - t
 
     t2 = sample(2)
-    per_step_budget = 150.0 / max(1, args.steps + args.warmup)
+    per_step_budget = args.ref_seconds / max(1, args.steps + args.warmup)
     nts = int(max(2, min(50, per_step_budget / max(t2, 1e-3)))) + 1
     for _ in range(args.warmup):
         sample(2)
@@ -852,6 +857,8 @@ def main():
                     choices=["forward", "so16", "precision", "diffusion", "fwi", "decomp",
                              "tblock"])
     ap.add_argument("--nt", type=int, default=1000)
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="host-time budget of the --impl reference run (oracle steps per step)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")

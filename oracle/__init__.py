@@ -71,6 +71,7 @@ def _load():
             lib.orc_dt_max.argtypes = [ctypes.c_int, _D, ctypes.c_int, ctypes.c_double]
             lib.orc_dt_max.restype = ctypes.c_double
             lib.orc_extend_model.argtypes = [_SP, _D, _D]
+            lib.orc_fold_model.argtypes = [_SP, _D, _D]
             lib.orc_damping.argtypes = [_SP, ctypes.c_double, _D]
             lib.orc_interp.argtypes = [_SP, ctypes.c_int, _D, _I64, _D]
             lib.orc_forward.argtypes = [_SP, _D, _D, ctypes.c_int, _D, _D, ctypes.c_int, _D, _D, _D, _D]
@@ -157,6 +158,16 @@ def extend_model(setup: Setup, m_phys) -> np.ndarray:
     out = np.empty(setup.comp_shape)
     s = setup._c()
     _check(_load().orc_extend_model(ctypes.byref(s), _dp(m_phys), _dp(out)))
+    return out
+
+
+def fold_model(setup: Setup, g_comp) -> np.ndarray:
+    """Adjoint of ``extend_model``: a computational-grid field (the gradient
+    with respect to the extended model) summed onto the physical model."""
+    g_comp = _f64(g_comp, setup.comp_shape)
+    out = np.empty(setup.shape)
+    s = setup._c()
+    _check(_load().orc_fold_model(ctypes.byref(s), _dp(g_comp), _dp(out)))
     return out
 
 

@@ -194,6 +194,38 @@ int orc_extend_model(const orc_setup *s, const double *m_phys, double *m_comp)
 }
 
 /*
+ * Adjoint of orc_extend_model (the gradient with respect to the physical
+ * model): every computational point adds its value into the physical point
+ * whose value the extension repeats there, so that for any m_phys and g_comp
+ *   <extend(m_phys), g_comp> = <m_phys, fold(g_comp)>.
+ * g_phys has the physical shape and is overwritten.
+ */
+int orc_fold_model(const orc_setup *s, const double *g_comp, double *g_phys)
+{
+    if (check_setup(s) != ORC_OK || !g_comp || !g_phys) return ORC_ERR_ARG;
+    int64_t n[3];
+    comp_shape(s, n);
+    int64_t np[3] = {1, 1, 1};
+    for (int a = 0; a < s->ndim; ++a) np[a] = s->shape[a];
+    int64_t total = n[0] * n[1] * n[2];
+    memset(g_phys, 0, sizeof(double) * (size_t)(np[0] * np[1] * np[2]));
+    int nd = s->ndim;
+    for (int64_t idx = 0; idx < total; ++idx) {
+        int64_t i[3];
+        unravel(nd, n, idx, i);
+        int64_t dst = 0;
+        for (int a = 0; a < nd; ++a) {
+            int64_t k = i[a] - s->nbl;
+            if (k < 0) k = 0;
+            if (k > np[a] - 1) k = np[a] - 1;
+            dst = dst * np[a] + k;
+        }
+        g_phys[dst] += g_comp[idx];
+    }
+    return ORC_OK;
+}
+
+/*
  * Damping field eta of the absorbing layer (Sec. 5, Eq. 3: "spatially varying
  * dampening factor"; Sec. 5.4: 40 layer points on each side).  Quadratic
  * profile, one term per axis, zero in the physical domain.

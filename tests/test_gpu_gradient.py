@@ -116,17 +116,11 @@ def test_autograd_function_matches_oracle(fw):
     loss = 0.5 * ((rec - d) ** 2).sum()
     loss.backward()
     g = m.grad.detach().cpu().numpy()
-    # oracle: gradient w.r.t. the computational model, folded onto the physical edges
+    # oracle: gradient w.r.t. the computational model, folded onto the
+    # physical model (the adjoint of the model extension)
+    import oracle
     ref = pb.oracle_gradient((rec.detach() - d).cpu().numpy().astype(np.float64))
-    nbl = pb.nbl
-    fold = np.zeros(pb.shape)
-    n = ref.shape
-    for x in range(n[0]):
-        for y in range(n[1]):
-            cx = min(max(x - nbl, 0), pb.shape[0] - 1)
-            cy = min(max(y - nbl, 0), pb.shape[1] - 1)
-            cz = np.clip(np.arange(n[2]) - nbl, 0, pb.shape[2] - 1)
-            np.add.at(fold[cx, cy], cz, ref[x, y])
+    fold = oracle.fold_model(pb.setup, ref)
     s.close()
     assert rel_l2(g, fold) < 1e-4
 

@@ -187,16 +187,10 @@ def test_gradient_residual_difference_and_physical_layout(fw):
     s.close()
     ref = pb.oracle_gradient(a.astype(np.float64) - b)
     assert rel_l2(g_comp, ref) < TOL
-    # fold the oracle's layer gradient onto the physical edge cells
-    nbl = pb.nbl
-    fold = np.zeros(pb.shape)
-    n = ref.shape
-    for x in range(n[0]):
-        for y in range(n[1]):
-            cx = min(max(x - nbl, 0), pb.shape[0] - 1)
-            cy = min(max(y - nbl, 0), pb.shape[1] - 1)
-            cz = np.clip(np.arange(n[2]) - nbl, 0, pb.shape[2] - 1)
-            np.add.at(fold[cx, cy], cz, ref[x, y])
+    # the physical-layout gradient is the oracle's computational gradient
+    # folded onto the physical model (the adjoint of the model extension)
+    import oracle
+    fold = oracle.fold_model(pb.setup, ref)
     assert rel_l2(g_phys, fold) < TOL
 
 

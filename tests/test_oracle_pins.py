@@ -442,3 +442,61 @@ def test_diffusion_matches_generated_code_constants():
                        + wc * u0[1:-1, 1:-1])
     assert np.allclose(u1, ref, rtol=0, atol=1e-12)
     assert g["interior_first"] == 1 and g["interior_last"] == g["nx"] - 2
+
+
+# ---------------------------------------------------------------- model extension
+# The paper gives only "40 points of damping layer" (Sec. 5.4); the reading is
+# that the model is extended into the layer by repeating its edge values, and
+# the gradient with respect to the physical model is the adjoint (transpose)
+# of that extension.  The index maps below are spelled out by hand for
+# nbl = 2: computational index i takes physical index clamp(i - 2), so a
+# physical axis of 3 points becomes [0,0,0,1,2,2,2] and one of 4 points
+# [0,0,0,1,2,3,3,3].  A clamp shifted by one changes these lists.
+_MAP3 = [0, 0, 0, 1, 2, 2, 2]
+_MAP4 = [0, 0, 0, 1, 2, 3, 3, 3]
+
+
+def test_extend_model_2d_spelled_out():
+    m = np.arange(1.0, 13.0).reshape(3, 4) ** 1.5   # non-constant, all values distinct
+    s = oracle.Setup((3, 4), 10.0, 4, 2, 1.0, 2)
+    M = oracle.extend_model(s, m)
+    assert M.shape == (7, 8)
+    for i in range(7):
+        for k in range(8):
+            assert M[i, k] == m[_MAP3[i], _MAP4[k]], (i, k)
+
+
+def test_extend_model_3d_spelled_out():
+    rng = np.random.default_rng(12)
+    m = rng.uniform(0.1, 0.5, (3, 3, 4))
+    s = oracle.Setup((3, 3, 4), 10.0, 4, 2, 1.0, 2)
+    M = oracle.extend_model(s, m)
+    assert M.shape == (7, 7, 8)
+    for i in range(7):
+        for j in range(7):
+            for k in range(8):
+                assert M[i, j, k] == m[_MAP3[i], _MAP3[j], _MAP4[k]], (i, j, k)
+
+
+def test_fold_model_counts_repetitions():
+    # folding a field of ones counts how many computational points repeat
+    # each physical point: (nbl + 1) at an edge, 1 inside, per axis
+    s = oracle.Setup((3, 4), 10.0, 4, 2, 1.0, 2)
+    f = oracle.fold_model(s, np.ones((7, 8)))
+    cx = [3, 1, 3]
+    cz = [3, 1, 1, 3]
+    assert np.array_equal(f, np.outer(cx, cz).astype(float))
+    s3 = oracle.Setup((3, 3, 4), 10.0, 4, 2, 1.0, 2)
+    f3 = oracle.fold_model(s3, np.ones((7, 7, 8)))
+    assert np.array_equal(f3, np.einsum("i,j,k->ijk", cx, cx, cz).astype(float))
+
+
+@pytest.mark.parametrize("shape,nbl", [((3, 4), 2), ((3, 3, 4), 2), ((5, 2, 6), 3), ((7, 9), 0)])
+def test_fold_is_adjoint_of_extension(shape, nbl):
+    rng = np.random.default_rng(len(shape) * 10 + nbl)
+    s = oracle.Setup(shape, 10.0, 4, nbl, 1.0, 2)
+    m = rng.standard_normal(shape)
+    g = rng.standard_normal(s.comp_shape)
+    a = float(np.sum(oracle.extend_model(s, m) * g))
+    b = float(np.sum(m * oracle.fold_model(s, g)))
+    assert abs(a - b) <= 1e-13 * max(abs(a), 1.0)
