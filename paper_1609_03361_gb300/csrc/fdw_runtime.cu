@@ -30,6 +30,7 @@
 #include <tuple>
 #include <vector>
 
+#include "fdw_host.h"
 #include "fdw_internal.h"
 #include "fdw_tb.h"
 #include "fdwave.h"
@@ -53,10 +54,20 @@ static void cuda_check(cudaError_t e, const char* what) {
 }
 #define CK(call) cuda_check((call), #call)
 
+static bool env_flag(const char* name) {
+  const char* v = std::getenv(name);
+  return v && *v && std::strcmp(v, "0") != 0;
+}
+
+// Test hook: while the environment variable FDW_TEST_FAIL_ALLOC is set (and
+// not "0"), every device allocation of the library fails as an exhausted
+// device would, without calling the allocator, so that the tests can check
+// that a failed allocation reports FDW_ERR_OOM and leaves the context usable.
 template <class T>
 static T* dalloc(size_t count) {
   void* p = nullptr;
   if (count == 0) count = 1;
+  if (env_flag("FDW_TEST_FAIL_ALLOC")) fail(FDW_ERR_OOM, "cudaMalloc: out of device memory (test hook)");
   cuda_check(cudaMalloc(&p, count * sizeof(T)), "cudaMalloc");
   return static_cast<T*>(p);
 }
@@ -65,90 +76,14 @@ static void dfree(void* p) {
   if (p) cudaFree(p);
 }
 
-// ---------------------------------------------------------------- host math
-
-// Second-derivative weights at offsets 0..r of the 2r+1 point central stencil,
-// by Fornberg's recursion (Math. Comp. 51, 1988) on the nodes 0, 1, -1, 2, -2, ...
-static std::vector<double> fornberg_second_derivative(int p) {
-  const int r = p / 2;
-  const int N = 2 * r + 1;
-  std::vector<double> x(N);
-  x[0] = 0.0;
-  for (int j = 1; j <= r; ++j) {
-    x[2 * j - 1] = j;
-    x[2 * j] = -j;
-  }
-  const int M = 2;
-  // d[m][n][v] flattened
-  std::vector<double> d((M + 1) * N * N, 0.0);
-  auto D = [&](int m, int n, int v) -> double& { return d[(m * N + n) * N + v]; };
-  D(0, 0, 0) = 1.0;
-  double c1 = 1.0;
-  for (int n = 1; n < N; ++n) {
-    double c2 = 1.0;
-    for (int v = 0; v < n; ++v) {
-      const double c3 = x[n] - x[v];
-      c2 *= c3;
-      for (int m = 0; m <= std::min(n, M); ++m) {
-        const double lower = m ? D(m - 1, n - 1, v) : 0.0;
-        D(m, n, v) = (x[n] * D(m, n - 1, v) - m * lower) / c3;
-      }
-    }
-    for (int m = 0; m <= std::min(n, M); ++m) {
-      const double lower = m ? D(m - 1, n - 1, n - 1) : 0.0;
-      D(m, n, n) = c1 / c2 * (m * lower - x[n - 1] * D(m, n - 1, n - 1));
-    }
-    c1 = c2;
-  }
-  std::vector<double> c(r + 1);
-  c[0] = D(M, N - 1, 0);
-  for (int j = 1; j <= r; ++j) c[j] = 0.5 * (D(M, N - 1, 2 * j - 1) + D(M, N - 1, 2 * j));
-  return c;
-}
-
-static bool valid_order(int p) { return p >= 2 && p <= 16 && p % 2 == 0; }
-
-static double symbol_max(int p) {
-  const std::vector<double> c = fornberg_second_derivative(p);
-  double s = c[0];
-  for (int j = 1; j <= p / 2; ++j) s += 2.0 * ((j % 2) ? -1.0 : 1.0) * c[j];
-  return std::fabs(s);
-}
-
-static double dt_limit(int ndim, const double* h, int p, double vmax) {
-  const double S = symbol_max(p);
-  double acc = 0.0;
-  for (int a = 0; a < ndim; ++a) acc += S / (h[a] * h[a]);
-  return 2.0 / (vmax * std::sqrt(acc));
-}
-
 // ---------------------------------------------------------------- TMA maps
-
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !p) fail(FDW_ERR_CUDA, "cuTensorMapEncodeTiled not found");
-    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
 
 // Pitched field(s) [slots][nx][ny][nzp] of element type dt; rank 3 when slots == 0.
 static void make_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void* base,
                      int nx, int ny, int nz, int nzp, int slots, long long slot_elems, int box_z,
                      int box_y) {
-  cuuint64_t dims[4] = {(cuuint64_t)nz, (cuuint64_t)ny, (cuuint64_t)nx, (cuuint64_t)(slots ? slots : 1)};
-  cuuint64_t strides[3] = {(cuuint64_t)nzp * esize, (cuuint64_t)nzp * ny * esize,
-                           (cuuint64_t)slot_elems * esize};
-  cuuint32_t box[4] = {(cuuint32_t)box_z, (cuuint32_t)box_y, 1, 1};
-  cuuint32_t estr[4] = {1, 1, 1, 1};
-  const cuuint32_t rank = slots ? 4 : 3;
-  CUresult r = encode_fn()(map, dt, rank, const_cast<void*>(base), dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUresult r = encode_field_map(map, dt, esize, base, nx, ny, nz, nzp, slots, slot_elems,
+                                      box_z, box_y);
   if (r != CUDA_SUCCESS) {
     std::ostringstream os;
     os << "cuTensorMapEncodeTiled failed (" << (int)r << ") dims " << nz << "x" << ny << "x" << nx
@@ -158,20 +93,6 @@ static void make_map(CUtensorMap* map, CUtensorMapDataType dt, int esize, const 
 }
 
 // ---------------------------------------------------------------- kernels
-
-static const void* step_fn(int r, int tile, bool grad) {
-  switch (r) {
-    case 1: return step_kernel_r1(tile, grad);
-    case 2: return step_kernel_r2(tile, grad);
-    case 3: return step_kernel_r3(tile, grad);
-    case 4: return step_kernel_r4(tile, grad);
-    case 5: return step_kernel_r5(tile, grad);
-    case 6: return step_kernel_r6(tile, grad);
-    case 7: return step_kernel_r7(tile, grad);
-    case 8: return step_kernel_r8(tile, grad);
-  }
-  return nullptr;
-}
 
 static int device_sms(int dev) {
   int v = 0;
@@ -183,11 +104,6 @@ static int device_smem_optin(int dev) {
   int v = 0;
   CK(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   return v;
-}
-
-static bool env_flag(const char* name) {
-  const char* v = std::getenv(name);
-  return v && *v && std::strcmp(v, "0") != 0;
 }
 
 }  // namespace fdw
@@ -409,21 +325,13 @@ struct fdw_batch {
 
 static int msize(int t) { return t == kF32 ? 4 : 2; }
 
-static bool is_device_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes a;
-  cudaError_t e = cudaPointerGetAttributes(&a, p);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 static void* staging_buf(fdw_ctx* c, int key, size_t bytes) {
   auto it = c->staging.find(key);
   if (it != c->staging.end() && it->second.second >= bytes) return it->second.first;
-  if (it != c->staging.end()) dfree(it->second.first);
+  if (it != c->staging.end()) {  // dropped first: a failed allocation leaves no stale entry
+    dfree(it->second.first);
+    c->staging.erase(it);
+  }
   void* p = dalloc<unsigned char>(bytes);
   c->staging[key] = {p, bytes};
   return p;
@@ -451,6 +359,17 @@ static void set_device(int dev) { CK(cudaSetDevice(dev)); }
 
 // ---------------------------------------------------------------- points
 
+static GridGeom ctx_geom(const fdw_ctx* c) {
+  GridGeom g;
+  g.ndim = c->ndim;
+  g.nbl = c->nbl;
+  for (int a = 0; a < 3; ++a) {
+    g.phys[a] = c->phys[a];
+    g.h[a] = c->h[a];
+  }
+  return g;
+}
+
 // samples: the set is sampled (receivers of the forward step) rather than
 // injected; it decides which points a slab keeps.
 static void compute_points(fdw_ctx* c, PointSet& ps, int n, const double* xyz, bool samples) {
@@ -461,25 +380,17 @@ static void compute_points(fdw_ctx* c, PointSet& ps, int n, const double* xyz, b
   out.base.resize((size_t)n * 3);
   out.w.resize((size_t)n * 8);
   // internal axes: 3D (x, y, z); 2D (x, -, z) with user axes (x, z)
+  const GridGeom g = ctx_geom(c);
   for (int j = 0; j < n; ++j) {
-    int b[3] = {0, 0, 0};
-    double f[3] = {0, 0, 0};
-    for (int a = 0; a < 3; ++a) {
-      if (c->ndim == 2 && a == 1) continue;
-      const int ua = (c->ndim == 2 && a == 2) ? 1 : a;
-      const double xv = xyz[(size_t)j * c->ndim + ua];
-      const double top = (double)(c->phys[a] - 1) * c->h[a];
-      if (!(xv >= 0.0) || !(xv <= top)) {
-        std::ostringstream os;
-        os << "point " << j << " coordinate " << ua << " = " << xv << " outside [0, " << top << "]";
-        fail(FDW_ERR_OUT_OF_DOMAIN, os.str());
-      }
-      const double xi = xv / c->h[a];
-      long long i = (long long)std::floor(xi);
-      if (i < 0) i = 0;
-      if (i > c->phys[a] - 2) i = c->phys[a] - 2;
-      b[a] = (int)i + c->nbl;
-      f[a] = xi - (double)i;
+    int b[3];
+    double f[3];
+    const int bad = locate_point(g, xyz + (size_t)j * c->ndim, b, f);
+    if (bad >= 0) {
+      const int ia = (c->ndim == 2 && bad == 1) ? 2 : bad;
+      std::ostringstream os;
+      os << "point " << j << " coordinate " << bad << " = " << xyz[(size_t)j * c->ndim + bad]
+         << " outside [0, " << (double)(c->phys[ia] - 1) * c->h[ia] << "]";
+      fail(FDW_ERR_OUT_OF_DOMAIN, os.str());
     }
     // a slab keeps local x indices: a source keeps the corners in its planes,
     // a receiver is kept whole by the slab that owns its base plane (its
@@ -495,13 +406,11 @@ static void compute_points(fdw_ctx* c, PointSet& ps, int n, const double* xyz, b
     }
     for (int a = 0; a < 3; ++a) out.base[(size_t)j * 3 + a] = (c->ndim == 2 && a == 1) ? 0 : b[a];
     for (int cc = 0; cc < 8; ++cc) {
-      const int bx = (cc >> 2) & 1, by = (cc >> 1) & 1, bz = cc & 1;
-      double w = (bx ? f[0] : 1.0 - f[0]) * (bz ? f[2] : 1.0 - f[2]);
-      if (c->ndim == 3) w *= by ? f[1] : 1.0 - f[1];
-      else if (by) w = 0.0;
-      if (!keep_point) w = 0.0;
-      if (c->slab && !samples && (b[0] + bx < c->own0 || b[0] + bx >= c->own1)) w = 0.0;
-      out.w[(size_t)j * 8 + cc] = (float)w;
+      const int bx = (cc >> 2) & 1;
+      float w = corner_weight(g, f, cc);
+      if (!keep_point) w = 0.f;
+      if (c->slab && !samples && (b[0] + bx < c->own0 || b[0] + bx >= c->own1)) w = 0.f;
+      out.w[(size_t)j * 8 + cc] = w;
     }
     if (c->slab && !samples) {  // a base outside the slab: keep it inside (weights are zero)
       const int bxl = out.base[(size_t)j * 3];
@@ -509,10 +418,15 @@ static void compute_points(fdw_ctx* c, PointSet& ps, int n, const double* xyz, b
     }
   }
   if (n > 0) {
-    out.d_base = dalloc<int>((size_t)n * 3);
-    out.d_w = dalloc<float>((size_t)n * 8);
-    CK(cudaMemcpy(out.d_base, out.base.data(), sizeof(int) * n * 3, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(out.d_w, out.w.data(), sizeof(float) * n * 8, cudaMemcpyHostToDevice));
+    try {  // the context keeps its previous points if this fails
+      out.d_base = dalloc<int>((size_t)n * 3);
+      out.d_w = dalloc<float>((size_t)n * 8);
+      CK(cudaMemcpy(out.d_base, out.base.data(), sizeof(int) * n * 3, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(out.d_w, out.w.data(), sizeof(float) * n * 8, cudaMemcpyHostToDevice));
+    } catch (...) {
+      out.release();
+      throw;
+    }
   }
   ps.release();
   ps = std::move(out);
@@ -521,56 +435,6 @@ static void compute_points(fdw_ctx* c, PointSet& ps, int n, const double* xyz, b
 
 // ---------------------------------------------------------------- plan
 
-// Shared-memory stages of a step launch.  The forward and adjoint steps stage
-// each plane's tiles with its halo plane; the gradient step, whose tiles are
-// twice the halo plane, keeps them in a second ring of stages that is only
-// occupied while they are in flight (the halo ring also holds the r planes of
-// the x stencil ahead of the plane being updated).
-struct StageLayout {
-  int off_p, off_m, off_f, off_a, off_e;  // tile offsets inside their stage
-  int bytes;    // halo-ring stage
-  int cbytes;   // second-ring stage (0: no second ring)
-  int r;
-};
-
-static int round128(int x) { return (x + 127) & ~127; }
-
-// Stages of the second ring for `stages` halo stages: the tiles of plane x
-// are issued with the halo plane x + r, so at most stages - r are in flight.
-static int second_ring_stages(const StageLayout& L, int stages) {
-  return L.cbytes ? std::max(2, stages - L.r) : 0;
-}
-
-static StageLayout stage_layout(int r, int tile, int mt_bytes, bool grad, bool etaf) {
-  const bool split = grad || kTiles[tile].split;
-  const int TY = tile_rows(kTiles[tile]);
-  const int R4 = (r + 3) & ~3;
-  const int ZW = kTZ + 2 * R4, YW = TY + 2 * r;
-  StageLayout L;
-  L.r = r;
-  const int halo = round128(YW * ZW * 4);
-  int off = split ? 0 : halo;
-  L.off_p = off;
-  off += round128(TY * kTZ * 4);
-  L.off_m = off;
-  off += round128(TY * kTZ * mt_bytes);
-  L.off_f = off;
-  if (grad) off += round128(TY * kTZ * 4);
-  L.off_a = off;
-  if (grad) off += round128(TY * kTZ * 4);
-  L.off_e = off;
-  if (etaf) off += round128(TY * kTZ * 4);
-  L.bytes = split ? halo : off;
-  L.cbytes = split ? off : 0;
-  return L;
-}
-
-static size_t smem_bytes(const StageLayout& L, int stages) {
-  const int sc = second_ring_stages(L, stages);
-  return (size_t)stages * L.bytes + (size_t)sc * L.cbytes + (size_t)(2 * stages + 2 * sc + 1) * 8 +
-         128;
-}
-
 static int plan_mtype(const Plan& pl) { return pl.shots[0]->mtype; }
 static bool plan_etaf(const Plan& pl) {
   for (auto* c : pl.shots)
@@ -578,13 +442,7 @@ static bool plan_etaf(const Plan& pl) {
   return false;
 }
 
-static void configure_kernel(const void* fn, size_t smem) {
-  CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // all of the unified L1 / shared memory as shared memory: the pipeline
-  // stages are the working set, the kernel reads little through L1
-  CK(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                          (int)cudaSharedmemCarveoutMaxShared));
-}
+static void configure_kernel(const void* fn, size_t smem) { CK(raise_smem_limit(fn, smem)); }
 
 // Occupancy-limited number of resident CTAs of a launch.
 static int resident_ctas(const Plan& pl, int tile, int stages, bool grad) {
@@ -637,6 +495,7 @@ static void choose_default_tiling(Plan& pl) {
 
 static void upload_vec(void** dptr, const void* src, size_t bytes) {
   dfree(*dptr);
+  *dptr = nullptr;
   *dptr = dalloc<unsigned char>(bytes);
   if (bytes) CK(cudaMemcpy(*dptr, src, bytes, cudaMemcpyHostToDevice));
 }
@@ -660,7 +519,7 @@ static void build_lists(Plan& pl) {
   std::vector<std::array<int, 2>> cols(pl.shots.size());
   for (size_t s = 0; s < pl.shots.size(); ++s) {
     const fdw_ctx* c = pl.shots[s];
-    cols[s] = {(c->ny + TY - 1) / TY, (c->nz + kTZ - 1) / kTZ};
+    column_tiles(c->ny, c->nz, TY, &cols[s][0], &cols[s][1]);
     for (int x0 = c->own0; x0 < c->own1; x0 += pl.lx)  // a slab's ghost planes are not updated
       rows.push_back(Row{(int)s, x0, std::min(c->own1, x0 + pl.lx), 0, false});
   }
@@ -720,13 +579,7 @@ static void build_lists(Plan& pl) {
     for (size_t q = 0; q < order.size(); ++q) {
       const int li = order[q];
       pos[ri][li] = (int)q;
-      Unit u{};
-      u.shot = r.shot;
-      u.x0 = r.x0;
-      u.x1 = r.x1;
-      u.y0 = (li / ck) * TY;
-      u.z0 = (li % ck) * kTZ;
-      pl.units.push_back(u);
+      pl.units.push_back(make_unit(r.shot, r.x0, r.x1, li, ck, TY));
     }
   }
   const int U = (int)pl.units.size();
@@ -748,9 +601,11 @@ static void build_lists(Plan& pl) {
   for (int role = 0; role < kNumRoles; ++role) {
     RoleLists& L = pl.lists[role];
     L = RoleLists();
-    // injection: (unit, x, y, z) -> terms (j, w), deterministic order
-    std::map<std::tuple<int, int, int, int>, std::vector<InjTerm>> inj;
-    std::vector<std::vector<int>> smp(U);
+    // injection: terms (j, w) grouped by node (unit, x, y, z), deterministic order
+    std::vector<Corner> corners;
+    // sampling: the sampled points of all shots, each with the unit that
+    // records it (-1: none), numbered per shot
+    std::vector<int> smp_unit, smp_j;
     for (size_t s = 0; s < pl.shots.size(); ++s) {
       const fdw_ctx* c = pl.shots[s];
       const PointSet& ip = (role == kRoleAdj) ? c->rec : c->src;
@@ -765,36 +620,32 @@ static void build_lists(Plan& pl) {
           // has no adjoint step
           const int un = unit_of((int)s, x, y, z);
           if (un < 0) continue;
-          inj[std::make_tuple(un, x, y, z)].push_back(InjTerm{j, w});
+          corners.push_back(Corner{un, x, y, z, j, w});
         }
       if (role != kRoleRec) {
         const PointSet& sp = (role == kRoleAdj) ? c->src : c->rec;
         for (int j = 0; j < sp.n; ++j) {
           const int* b = &sp.base[(size_t)j * 3];
-          const int un = unit_of((int)s, b[0], b[1], b[2]);
-          if (un >= 0) smp[un].push_back(j);
+          smp_unit.push_back(unit_of((int)s, b[0], b[1], b[2]));
+          smp_j.push_back(j);
         }
       }
     }
+    L.nodes.resize(corners.size());
+    L.terms.resize(corners.size());
     L.inj_ptr.assign(U + 1, 0);
-    for (auto& kv : inj) {
-      InjNode nd{};
-      nd.x = std::get<1>(kv.first);
-      nd.y = std::get<2>(kv.first);
-      nd.z = std::get<3>(kv.first);
-      nd.tbeg = (int)L.terms.size();
-      for (auto& t2 : kv.second) L.terms.push_back(t2);
-      nd.tend = (int)L.terms.size();
-      L.nodes.push_back(nd);
-      L.node_shot.push_back(pl.units[std::get<0>(kv.first)].shot);
-      L.inj_ptr[std::get<0>(kv.first) + 1]++;
-    }
-    for (int u = 0; u < U; ++u) L.inj_ptr[u + 1] += L.inj_ptr[u];
+    const int nn = group_corners(corners.data(), (int)corners.size(), U, L.nodes.data(),
+                                 L.terms.data(), L.inj_ptr.data());
+    L.nodes.resize(nn);
+    for (int u = 0; u < U; ++u)
+      for (int i = L.inj_ptr[u]; i < L.inj_ptr[u + 1]; ++i) L.node_shot.push_back(pl.units[u].shot);
+    // units belong to one shot each, so a unit's list holds one shot's points
     L.smp_ptr.assign(U + 1, 0);
-    for (int u = 0; u < U; ++u) {
-      L.smp_ptr[u + 1] = L.smp_ptr[u] + (int)smp[u].size();
-      for (int j : smp[u]) L.smp_pts.push_back(j);
-    }
+    L.smp_pts.resize(smp_unit.size());
+    const int ns = bucket_points(smp_unit.data(), (int)smp_unit.size(), U, L.smp_ptr.data(),
+                                 L.smp_pts.data());
+    L.smp_pts.resize(ns);
+    for (int& k : L.smp_pts) k = smp_j[k];
     upload_vec((void**)&L.d_inj_ptr, L.inj_ptr.data(), L.inj_ptr.size() * sizeof(int));
     upload_vec((void**)&L.d_smp_ptr, L.smp_ptr.data(), L.smp_ptr.size() * sizeof(int));
     upload_vec((void**)&L.d_smp_pts, L.smp_pts.data(), L.smp_pts.size() * sizeof(int));
@@ -882,6 +733,8 @@ static void ensure_tickets(Plan& pl, long long cap) {
   if (cap > (1LL << 30)) fail(FDW_ERR_ARG, "too many step launches in one pass");
   pl.clear_graphs();
   dfree(pl.d_tickets);
+  pl.d_tickets = nullptr;
+  pl.ticket_cap = 0;
   pl.d_tickets = dalloc<int>((size_t)cap);
   CK(cudaMemset(pl.d_tickets, 0, sizeof(int) * (size_t)cap));
   pl.ticket_cap = (int)cap;
@@ -901,12 +754,16 @@ static void ensure_plan(Plan& pl) {
   const std::vector<int> v = current_versions(pl);
   if (pl.built && v == pl.built_versions) return;
   if (!pl.built) choose_default_tiling(pl);
+  // a rebuild that fails part-way (an allocation) leaves the plan marked
+  // unbuilt, so the next call rebuilds it from scratch
+  pl.built = false;
   build_lists(pl);
   pl.tb.release();
   for (int role = 0; role < kNumRoles; ++role) {
     pl.hdesc[role].clear();
     for (auto* c : pl.shots) pl.hdesc[role].push_back(make_desc(pl, c, role));
     dfree(pl.d_desc[role]);
+    pl.d_desc[role] = nullptr;
     pl.d_desc[role] = dalloc<ShotDesc>(pl.shots.size());
     CK(cudaMemcpy(pl.d_desc[role], pl.hdesc[role].data(), sizeof(ShotDesc) * pl.shots.size(),
                   cudaMemcpyHostToDevice));
@@ -1013,7 +870,10 @@ static void launch_adjoint_step(Plan& pl, StepArgs a, cudaStream_t s) {
 // zeros), the sum of the centre weights over the axes, and dt^2.
 static void stencil_weights(Plan& pl, float w[3][kMaxR + 1], float* csum, float* dt2) {
   const fdw_ctx* c0 = pl.shots[0];
-  if (pl.weights.empty()) pl.weights = fornberg_second_derivative(c0->order);
+  if (pl.weights.empty()) {
+    pl.weights.assign(c0->r + 1, 0.0);
+    fd_weights(c0->order, pl.weights.data());
+  }
   const double dt = c0->dt;
   *dt2 = (float)(dt * dt);
   const std::vector<double>& cw = pl.weights;
@@ -1876,9 +1736,11 @@ static void plan_sync(Plan& pl) {
     CK(cudaMemcpy(&e, pl.d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
       CK(cudaMemset(pl.d_err, 0, sizeof(int)));
+      const fdw_status st = device_error_status(e);
       std::ostringstream os;
-      os << "device-side wait timed out (code " << e << ")";
-      fail(FDW_ERR_TIMEOUT, os.str());
+      os << (st == FDW_ERR_TIMEOUT ? "device-side wait timed out" : "device-side fault")
+         << " (code " << e << ")";
+      fail(st, os.str());
     }
   }
 }
@@ -2050,8 +1912,7 @@ const char* fdw_status_string(fdw_status st) {
 fdw_status fdw_fd_weights(int space_order, double* c) {
   if (!valid_order(space_order)) return FDW_ERR_ORDER;
   if (!c) return FDW_ERR_ARG;
-  const std::vector<double> w = fornberg_second_derivative(space_order);
-  for (size_t i = 0; i < w.size(); ++i) c[i] = w[i];
+  fd_weights(space_order, c);
   return FDW_OK;
 }
 
@@ -2122,20 +1983,12 @@ static fdw_status create_ctx(fdw_ctx** out, int ndim, const int64_t* shape, cons
     // built-in damping profiles, eta * dt / 2
     std::vector<float> prof((size_t)c->nx + c->ny + c->nz, 0.f);
     const int n3[3] = {c->nx, c->ny, c->nz};
+    const GridGeom g = ctx_geom(c.get());
     size_t off = 0;
     for (int a = 0; a < 3; ++a) {
-      const bool active = !(ndim == 2 && a == 1);
       for (int il = 0; il < n3[a]; ++il) {
         const long long i = a == 0 ? il + c->gx0 : il;  // index in the full grid
-        double e = 0.0;
-        if (active && nbl > 0) {
-          const long long lo = nbl - i, hi = i - (nbl + c->phys[a] - 1);
-          const long long d = lo > 0 ? lo : (hi > 0 ? hi : 0);
-          const double emax = 3.0 * std::log(1000.0) / (2.0 * nbl * c->h[a] * vmax);
-          const double f = (double)d / nbl;
-          e = emax * f * f;
-        }
-        prof[off + il] = (float)(e * dt * 0.5);
+        prof[off + il] = damping_half_dt(g, a, i, vmax, dt);
       }
       off += n3[a];
     }
@@ -2181,7 +2034,8 @@ fdw_status fdw_set_model(fdw_ctx* c, const float* m, int layout, int m_dtype, vo
                          ? (size_t)c->phys[0] * c->phys[1] * c->phys[2]
                          : (size_t)c->nx_full * c->ny * c->nz;
     const float* md = device_in(c, 7, m, n, s);
-    if (m_dtype != c->mtype) {
+    if (m_dtype != c->mtype || !c->m) {  // no buffer: an earlier reallocation failed
+      c->model_set = false;  // until the new buffer holds a model
       dfree(c->m);
       c->m = nullptr;
       c->m = dalloc<unsigned char>((size_t)c->slot * msize(m_dtype));

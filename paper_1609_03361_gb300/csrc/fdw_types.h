@@ -118,6 +118,7 @@ struct StepParams {
   int* err;            // error word (0 = fine)
 };
 
-enum ErrBits : int { kErrTimeoutFull = 1, kErrTimeoutEmpty = 2, kErrBadUnit = 4 };
+// Bits of the device error word: a consumer (full) or producer (empty) wait gave up.
+enum ErrBits : int { kErrTimeoutFull = 1, kErrTimeoutEmpty = 2 };
 
 }  // namespace fdw

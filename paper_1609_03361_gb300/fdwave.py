@@ -391,19 +391,32 @@ def fdw_batch_get_tiling(b):
 
 def fdw_forward_static(shape, spacing, space_order, nbl, dt, nt, vmax, m, src_xyz, q, rec_xyz,
                        rec, stream=None, device=0):
-    """Allocation-free forward modelling of a small problem (see include/fdwave.h):
-    m, q and rec must be device arrays (torch CUDA tensors); coordinates are host."""
-    keep = []
+    """Allocation-free forward modelling of a small problem (see include/fdwave.h).
+
+    m (physical shape), q [nt][nsrc] and rec [nt][nrec] must be contiguous
+    float32 CUDA tensors on ``device``: the call writes the traces into ``rec``
+    itself, so no converted copy is made; coordinates are host arrays."""
+    torch = _torch()
     ndim = len(shape)
-    sh = (ctypes.c_int64 * ndim)(*[int(v) for v in shape])
-    sp = np.broadcast_to(np.asarray(spacing, dtype=np.float64), (ndim,)).copy()
     src = np.ascontiguousarray(src_xyz, dtype=np.float64).reshape(-1, ndim)
     rcv = np.ascontiguousarray(rec_xyz, dtype=np.float64).reshape(-1, ndim)
+    dev = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+    want = {"m": (m, int(np.prod([int(v) for v in shape]))), "q": (q, int(nt) * src.shape[0]),
+            "rec": (rec, int(nt) * rcv.shape[0])}
+    for name, (t, n) in want.items():
+        if not (_is_tensor(t) and t.is_cuda and t.device == dev and t.dtype == torch.float32
+                and t.is_contiguous()):
+            raise FdwError(1, f"{name} must be a contiguous float32 CUDA tensor on {dev}")
+        if t.numel() != n:
+            raise FdwError(1, f"{name} has {t.numel()} elements, expected {n}")
+    sh = (ctypes.c_int64 * ndim)(*[int(v) for v in shape])
+    sp = np.broadcast_to(np.asarray(spacing, dtype=np.float64), (ndim,)).copy()
     _check(lib().fdw_forward_static(ndim, sh, sp.ctypes.data_as(ctypes.POINTER(_D)),
                                     int(space_order), int(nbl), float(dt), int(nt), float(vmax),
-                                    _ptr(m, keep), src.shape[0], _ptr(src, keep, np.float64),
-                                    _ptr(q, keep), rcv.shape[0], _ptr(rcv, keep, np.float64),
-                                    _ptr(rec, keep), _stream(stream, device)))
+                                    m.data_ptr(), src.shape[0],
+                                    src.ctypes.data if src.size else None, q.data_ptr(),
+                                    rcv.shape[0], rcv.ctypes.data if rcv.size else None,
+                                    rec.data_ptr(), _stream(stream, dev)))
 
 
 def fdw_diffusion2d(u, tmp, dx, dy, alpha, dt, steps, steps_per_pass=0, stream=None):

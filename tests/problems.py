@@ -76,3 +76,16 @@ def rel_l2(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def assert_close(got, want, tol=1e-4, what=""):
+    """Parity of an FP32 result with the FP64 oracle: relative L2 error and the
+    largest point-wise error relative to the largest reference value, both
+    within tol (a local fault in one tile would hide in the norm alone)."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    scale = np.abs(want).max()
+    assert scale > 0, f"{what}: the reference is zero"
+    r = rel_l2(got, want)
+    e = float(np.abs(got - want).max() / scale)
+    assert r < tol and e <= tol, f"{what}: rel L2 {r:.3e}, max point-wise {e:.3e} (tol {tol:.0e})"

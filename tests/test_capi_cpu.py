@@ -99,3 +99,46 @@ def test_diffusion_host_checks(fw):
     assert f(16, 32, 2, 10, 0.1, 0.1, 1.0, lim, 3, 0, None) == 1          # nx < 3
     assert f(16, 32, 10, 10, 0.1, 0.1, -1.0, lim, 3, 0, None) == 1        # alpha <= 0
     assert f(None, 32, 10, 10, 0.1, 0.1, 1.0, lim, 3, 0, None) == 1       # null field
+
+
+# ---------------------------------------------------------------- allocation-free entry point
+# Every check below returns before the library makes any CUDA call: sizes,
+# order, stability and point locations are host logic, and a host buffer is
+# refused (FDW_ERR_ARG) instead of reaching a kernel as a device address.
+
+def _static(fw, shape, p, nbl, dt, nt, vmax, m, src, q, rec_xyz, rec):
+    import ctypes
+    ndim = len(shape)
+    sh = (ctypes.c_int64 * ndim)(*shape)
+    sp = (ctypes.c_double * ndim)(*([10.0] * ndim))
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, ndim)
+    rcv = np.ascontiguousarray(rec_xyz, dtype=np.float64).reshape(-1, ndim)
+    return fw.lib().fdw_forward_static(
+        ndim, sh, sp, p, nbl, dt, nt, vmax, m.ctypes.data, src.shape[0],
+        src.ctypes.data if src.size else None, q.ctypes.data, rcv.shape[0],
+        rcv.ctypes.data if rcv.size else None, rec.ctypes.data, None)
+
+
+def test_static_forward_host_checks(fw):
+    shape, p, nbl, nt, vmax = (20, 18, 22), 8, 4, 10, 2.0
+    dt = 0.9 * fw.fdw_dt_max(3, 10.0, p, vmax)
+    m = np.ones(shape, np.float32)
+    q = np.zeros((nt, 1), np.float32)
+    src = [[50.0, 50.0, 50.0]]
+    rec1 = [[60.0, 60.0, 60.0]]
+    out = np.zeros((nt, 1), np.float32)
+    # more receivers than the static tables hold (4096): FDW_ERR_SHAPE
+    many = np.tile(np.array(rec1), (4097, 1))
+    assert _static(fw, shape, p, nbl, dt, nt, vmax, m, src, q, many,
+                   np.zeros((nt, 4097), np.float32)) == 2
+    # a grid beyond 4096 computational points per axis: FDW_ERR_SHAPE
+    assert _static(fw, (5000, 4), 4, 0, dt, nt, vmax, m, [[1.0, 1.0]], q, [[2.0, 2.0]], out) == 2
+    # odd order, dt above the stability limit
+    assert _static(fw, shape, 7, nbl, dt, nt, vmax, m, src, q, rec1, out) == 3
+    assert _static(fw, shape, p, nbl, 1.01 * fw.fdw_dt_max(3, 10.0, p, vmax), nt, vmax, m, src, q,
+                   rec1, out) == 4
+    # a source or a receiver outside [0, (N-1) h]: FDW_ERR_OUT_OF_DOMAIN
+    assert _static(fw, shape, p, nbl, dt, nt, vmax, m, [[50.0, 171.0, 50.0]], q, rec1, out) == 5
+    assert _static(fw, shape, p, nbl, dt, nt, vmax, m, src, q, [[-0.5, 60.0, 60.0]], out) == 5
+    # every check passes but m, q and rec are host buffers: FDW_ERR_ARG
+    assert _static(fw, shape, p, nbl, dt, nt, vmax, m, src, q, rec1, out) == 1

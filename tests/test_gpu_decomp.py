@@ -2,11 +2,13 @@
 held by one process, ghost planes exchanged after every step.  Each slab runs
 the whole-grid step's arithmetic on its planes, so the summed traces and the
 slabs' own planes of the last wavefield must equal the whole-grid run bit for
-bit; sources and receivers sit on and across slab boundaries."""
+bit; sources and receivers sit on and across slab boundaries.  The summed
+traces and the wavefield reassembled from the slabs are also compared with the
+FP64 oracle (relative L2 and point-wise, 1e-4)."""
 import numpy as np
 import pytest
 
-from problems import Problem
+from problems import Problem, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -72,11 +74,19 @@ def test_slabs_equal_whole_grid(fw, shape, p, parts):
     nonzero = sum((np.abs(r.cpu().numpy()).sum(0) > 0).astype(int) for r in recs)
     assert np.all(nonzero[np.abs(rec_w).sum(0) > 0] == 1)
     r = p // 2
+    u_slabs = np.empty_like(u_w)
     for s, (b, e) in zip(sf.slabs, ranges):
         u = s.wavefield(0, like=q).cpu().numpy()
         assert u.shape[0] == e - b + 2 * r
         assert np.array_equal(u[r:r + e - b], u_w[b:e])
+        u_slabs[b:e] = u[r:r + e - b]
     sf.close()
+    # the decomposed run against the FP64 oracle on the whole grid
+    ref, uref = pb.oracle_forward(final=True)
+    assert np.abs(ref).max() > 0
+    for got, want in ((total, ref), (u_slabs, uref)):
+        assert rel_l2(got, want) < 1e-4
+        assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
 
 
 def test_slab_rejects_whole_loops(fw):

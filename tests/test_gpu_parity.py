@@ -7,7 +7,7 @@ Sizes span several tiles in y and z with ragged tails and several x chunks.
 import numpy as np
 import pytest
 
-from problems import Problem, rel_l2
+from problems import Problem, assert_close, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -39,8 +39,8 @@ def test_forward_3d_all_orders(fw, p):
     pb = Problem((37, 45, 29), 10.0, p, 8, 70, nsrc=2, nrec=9, seed=p)
     rec, u = _fwd(fw, pb)
     ref, uref = pb.oracle_forward(final=True)
-    assert rel_l2(rec, ref) < TOL
-    assert rel_l2(u, uref) < TOL
+    assert_close(rec, ref, TOL, "traces")
+    assert_close(u, uref, TOL, "wavefield")
 
 
 @pytest.mark.parametrize("tiling", [(0, 0, 0), (1, 0, 0), (2, 0, 0), (4, 0, 0), (5, 0, 0),
@@ -50,8 +50,8 @@ def test_forward_3d_tilings(fw, tiling):
     pb = Problem((40, 51, 35), 12.5, 8, 6, 60, nsrc=3, nrec=12, seed=11)
     rec, u = _fwd(fw, pb, tiling=tiling)
     ref, uref = pb.oracle_forward(final=True)
-    assert rel_l2(rec, ref) < TOL
-    assert rel_l2(u, uref) < TOL
+    assert_close(rec, ref, TOL, "traces")
+    assert_close(u, uref, TOL, "wavefield")
 
 
 def test_tilings_agree_bitwise(fw):
@@ -69,8 +69,8 @@ def test_forward_2d(fw, p):
     pb = Problem((61, 57), 10.0, p, 20, 200, nsrc=1, nrec=11, seed=3)
     rec, u = _fwd(fw, pb)
     ref, uref = pb.oracle_forward(final=True)
-    assert rel_l2(rec, ref) < TOL
-    assert rel_l2(u, uref) < TOL
+    assert_close(rec, ref, TOL, "traces")
+    assert_close(u, uref, TOL, "wavefield")
 
 
 def test_forward_ongrid_and_edge_points(fw):
@@ -158,10 +158,14 @@ def test_gradient_fp32_checkpoints(fw, k):
     assert rel_l2(g, ref) < TOL
 
 
-# k = 1 takes the separate max pass of the snapshot scale; k >= 2 folds the
-# maximum into the two steps that produce each pair
-@pytest.mark.parametrize("stype,tol,k", [("f16", 1e-2, 10), ("bf16", 5e-2, 10), ("f16", 1e-2, 1),
-                                         ("f16", 1e-2, 2), ("bf16", 5e-2, 3)])
+# FP16 snapshots (11-bit significand, one float32 scale per snapshot) keep the
+# gradient within 1e-3 of the FP64 oracle's exact gradient.  BF16 snapshots
+# (8-bit significand: 2^-9 relative rounding of every stored value) do not
+# reach 1e-3; their bound here is 5e-3.  k = 1 takes the separate max pass of
+# the snapshot scale; k >= 2 folds the maximum into the two steps that
+# produce each pair.
+@pytest.mark.parametrize("stype,tol,k", [("f16", 1e-3, 10), ("bf16", 5e-3, 10), ("f16", 1e-3, 1),
+                                         ("f16", 1e-3, 2), ("bf16", 5e-3, 3)])
 def test_gradient_low_precision_snapshots(fw, stype, tol, k):
     pb = Problem((29, 26, 31), 10.0, 8, 6, 90, nsrc=1, nrec=8, seed=32)
     resid = pb.oracle_forward().astype(np.float32)
@@ -171,7 +175,8 @@ def test_gradient_low_precision_snapshots(fw, stype, tol, k):
     s.sync()
     s.close()
     ref = pb.oracle_gradient(resid)
-    assert rel_l2(g, ref) < tol
+    err = rel_l2(g, ref)
+    assert err < tol, f"{stype} k={k}: gradient rel L2 {err:.3e} vs the FP64 oracle"
 
 
 def test_gradient_residual_difference_and_physical_layout(fw):
@@ -282,11 +287,13 @@ def test_config_2d_101_so4_500_steps(fw):
 @pytest.fixture(scope="module")
 def full_grid_case():
     """The 256^3 SO8 workload on its full 336^3 computational grid over its
-    first 24 steps, with the oracle's traces and last field (the oracle needs
-    about 1 s per step on this grid)."""
+    first 150 steps (the 15 Hz wavelet peaks at step 34; by step 150 the front
+    has crossed x-chunk and tile boundaries and entered the damping layer
+    above the source), with the oracle's traces and last field (the oracle
+    needs about 0.1 s per step on this grid on 16 cores)."""
     import oracle
     from paper_1609_03361_gb300 import workloads as W
-    nt = 24
+    nt = 150
     w = W.config_3d(256, 12.5, 8, nt)
     w.dt = W.choose_dt(oracle.dt_max(3, w.spacing, w.space_order, w.vmax))
     q = w.wavelet().astype(np.float32)[:, None]
@@ -316,9 +323,10 @@ def test_config_3d_256_so8_full_grid_first_steps(fw, full_grid_case, tiling):
     u = s.wavefield(0, like=q).cpu().numpy()
     s.sync()
     s.close()
-    assert np.abs(ref).max() > 0
-    assert rel_l2(rec, ref) < TOL
-    assert rel_l2(u, uref) < TOL
+    assert_close(rec, ref, TOL, "traces")
+    assert_close(u, uref, TOL, "wavefield")
+    # the front reached the layer above the source (depth index < nbl)
+    assert np.abs(uref[:, :, : w.nbl]).max() > 1e-3 * np.abs(uref).max()
 
 
 def test_batched_config_full_grids_first_steps(fw):
@@ -383,10 +391,11 @@ def test_single_step(fw):
 
 def test_config_3d_512_so16_full_grid_first_steps(fw):
     """The 512^3 SO16 workload on its full 592^3 computational grid (830 MB a
-    field) over its first 8 steps, FP32 model, against the oracle."""
+    field) over its first 40 steps, FP32 model, against the oracle: every
+    trace and the last field, relative L2 and point-wise."""
     import oracle
     from paper_1609_03361_gb300 import workloads as W
-    nt = 8
+    nt = 40
     w = W.config_3d(512, 12.5, 16, nt)
     w.dt = W.choose_dt(oracle.dt_max(3, w.spacing, 16, w.vmax))
     dev = torch.device("cuda", 0)
@@ -403,7 +412,5 @@ def test_config_3d_512_so16_full_grid_first_steps(fw):
     M = oracle.extend_model(st, w.m.astype(np.float32).astype(np.float64))
     ref, uref = oracle.forward(st, M, oracle.damping(st, w.vmax), w.src, q32.astype(np.float64),
                                w.rec, final=True)
-    assert np.abs(uref).max() > 0
-    assert rel_l2(u, uref) < TOL
-    if np.abs(ref).max() > 0:
-        assert rel_l2(rec, ref) < TOL
+    assert_close(u, uref, TOL, "wavefield")
+    assert_close(rec, ref, TOL, "traces")
