@@ -677,7 +677,7 @@ def run_fwi(nshots, nt, k, dev, group=4):
                        "grad_rel_l2_vs_plain_fp32": budget_diff}}
 
 
-def so16_measure(dev, steps=3, warmup=1, nt=2000):
+def so16_measure(dev, steps=3, warmup=1, nt=2000, tiling=None):
     """512^3 SO16 forward (592^3 computational), nt steps, FP32: GPts/s from
     CUDA events over `steps` whole runs after `warmup` runs, autotuned tiles,
     and the step kernel's HBM roofline fraction (16 B per point update)."""
@@ -693,7 +693,13 @@ def so16_measure(dev, steps=3, warmup=1, nt=2000):
     s.set_receivers(w.rec)
     q = torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev)
     rec = torch.empty((w.nt, w.rec.shape[0]), device=dev)
-    s.autotune(3)
+    if tiling:
+        s.set_tiling(*tiling)
+        s.set_model(torch.from_numpy(w.m.astype(np.float32)).to(dev))
+        s.set_sources(w.src)
+        s.set_receivers(w.rec)
+    else:
+        s.autotune(3)
     for _ in range(warmup):
         s.forward(q, rec)
     torch.cuda.synchronize(dev)
@@ -719,7 +725,8 @@ def so16_measure(dev, steps=3, warmup=1, nt=2000):
 
 
 def run_so16(args, dev):
-    r = so16_measure(dev, args.steps, args.warmup, args.nt if args.nt != 1000 else 2000)
+    tiling = tuple(int(v) for v in args.tiling.split(",")) if args.tiling else None
+    r = so16_measure(dev, args.steps, args.warmup, args.nt if args.nt != 1000 else 2000, tiling)
     line = {"metric": "GPts/s (SO-16 3D FP32 forward)", "value": r["gpts"], "unit": "GPts/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": r["ms_per_run"], "higher_is_better": True, "dtype": "f32",

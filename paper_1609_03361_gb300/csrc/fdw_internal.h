@@ -15,16 +15,24 @@ namespace fdw {
 // rotates; the others shift it (smaller code).  Tile 3 is meant for 2D grids.
 // Tile 6 is tile 4 with the per-plane tiles in a second ring: less shared
 // memory per CTA, which lets the high orders (r >= 6) hold three CTAs per SM.
+// Tiles 7 and 8 are tiles 4 and 6 with the x queue in tensor memory instead
+// of registers (no per-plane queue moves; the CTA allocates tq_cols columns).
 struct TileShape {
   int ny_pts;
   int warps;
   bool split;  // the forward and adjoint steps also keep the per-plane tiles
                // in a second ring (gradient steps always do)
+  bool tq;     // x queue in tensor memory
 };
-constexpr int kNumTiles = 7;
-constexpr TileShape kTiles[kNumTiles] = {{1, 4, false}, {2, 4, false}, {1, 8, false},
-                                         {1, 1, false}, {1, 4, false}, {2, 2, false},
-                                         {1, 4, true}};
+constexpr int kNumTiles = 9;
+constexpr TileShape kTiles[kNumTiles] = {{1, 4, false, false}, {2, 4, false, false},
+                                         {1, 8, false, false}, {1, 1, false, false},
+                                         {1, 4, false, false}, {2, 2, false, false},
+                                         {1, 4, true, false},  {1, 4, false, true},
+                                         {1, 4, true, true}};
+// Tensor-memory columns a CTA of a tq tile allocates at radius r (the ring of
+// 2 (2r+1) planes of four values, rounded up to a power of two); an SM has 512.
+__host__ __device__ constexpr int tq_columns(int r) { return 8 * (2 * r + 1) <= 128 ? 128 : 256; }
 constexpr int tile_rows(const TileShape& t) { return 4 * t.ny_pts * t.warps; }
 
 // Kernel registry: one translation unit per stencil radius.

@@ -444,15 +444,66 @@ static bool plan_etaf(const Plan& pl) {
 
 static void configure_kernel(const void* fn, size_t smem) { CK(raise_smem_limit(fn, smem)); }
 
+// Resident CTAs per SM of a step launch.  For tiles whose x queue lives in
+// tensor memory the runtime's occupancy query reports one CTA per SM (it
+// treats any kernel that allocates tensor memory that way), while the SM
+// holds as many as its registers, shared memory and threads allow (measured
+// on the GB300): count those directly.
+static int occupancy(const Plan& pl, int tile, const void* fn, int threads, size_t smem) {
+  int nb = 0;
+  if (!kTiles[tile].tq) {
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem));
+    return nb;
+  }
+  cudaFuncAttributes a;
+  CK(cudaFuncGetAttributes(&a, fn));
+  int regs_sm = 0, smem_sm = 0, reserved = 0, threads_sm = 0, blocks_sm = 0;
+  CK(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, pl.device));
+  CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, pl.device));
+  CK(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, pl.device));
+  CK(cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, pl.device));
+  CK(cudaDeviceGetAttribute(&blocks_sm, cudaDevAttrMaxBlocksPerMultiprocessor, pl.device));
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = ((a.numRegs + 7) / 8) * 8 * 32;   // allocated in units of 256 per warp
+  const int by_regs = regs_sm / (regs_warp * warps);
+  const int by_smem = (int)((size_t)smem_sm / (smem + a.sharedSizeBytes + (size_t)reserved));
+  const int by_threads = threads_sm / (warps * 32);
+  nb = std::min(std::min(by_regs, by_smem), std::min(by_threads, blocks_sm));
+  return std::min(nb, 512 / tq_columns(pl.r));
+}
+
+// Dynamic shared memory of a step launch: the stage rings, and for a tile
+// whose x queue lives in tensor memory, more if needed so that no more than
+// 512 / tq_columns(r) CTAs fit on an SM: each CTA allocates that many of the
+// SM's 512 columns, and a CTA that found too few free would wait in its
+// allocation until another CTA on the SM finished.
+static size_t launch_smem(const Plan& pl, int tile, const StageLayout& L, int stages,
+                          const void* fn, int threads) {
+  size_t smem = smem_bytes(L, stages);
+  configure_kernel(fn, smem);
+  if (!kTiles[tile].tq) return smem;
+  const int maxc = 512 / tq_columns(pl.r);
+  int smem_sm = 0, reserved = 0;
+  CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, pl.device));
+  CK(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, pl.device));
+  cudaFuncAttributes a;
+  CK(cudaFuncGetAttributes(&a, fn));
+  // the shared memory alone must keep a (maxc + 1)-th CTA out
+  const size_t need = (size_t)smem_sm / (maxc + 1) + 1 - a.sharedSizeBytes - reserved;
+  if (smem < need) smem = (need + 127) & ~size_t(127);
+  if (smem > (size_t)device_smem_optin(pl.device))
+    fail(FDW_ERR_ARG, "tensor-memory tile: cannot limit the CTAs per SM");
+  configure_kernel(fn, smem);
+  return smem;
+}
+
 // Occupancy-limited number of resident CTAs of a launch.
 static int resident_ctas(const Plan& pl, int tile, int stages, bool grad) {
   const StageLayout L = stage_layout(pl.r, tile, msize(plan_mtype(pl)), grad, plan_etaf(pl));
-  const size_t smem = smem_bytes(L, stages);
   const void* fn = step_fn(pl.r, tile, grad);
-  configure_kernel(fn, smem);
-  int nb = 0;
   const int threads = (kTiles[tile].warps + 1) * 32;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem));
+  const size_t smem = launch_smem(pl, tile, L, stages, fn, threads);
+  const int nb = occupancy(pl, tile, fn, threads, smem);
   return std::max(nb, 1) * device_sms(pl.device);
 }
 
@@ -791,10 +842,8 @@ static int grad_stages(Plan& pl) {
   const int cap = device_smem_optin(pl.device) - 1024;
   int best = pl.r + 2, best_nb = -1;
   for (int st = pl.r + 2; st <= 2 * pl.r + 8 && (int)smem_bytes(L, st) <= cap; ++st) {
-    const size_t smem = smem_bytes(L, st);
-    configure_kernel(fn, smem);
-    int nb = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem));
+    const size_t smem = launch_smem(pl, pl.tile, L, st, fn, threads);
+    const int nb = occupancy(pl, pl.tile, fn, threads, smem);
     if (nb >= best_nb) {
       best_nb = nb;
       best = st;
@@ -824,15 +873,13 @@ static const Plan::LaunchInfo& launch_info(Plan& pl, bool grad) {
   if (it != pl.launch_cache.end()) return it->second;
   const StageLayout L = stage_layout(pl.r, pl.tile, msize(mt), grad, etaf);
   Plan::LaunchInfo li;
-  li.smem = smem_bytes(L, stages);
   li.stages = stages;
   li.cstages = second_ring_stages(L, stages);
   li.cstage_bytes = L.cbytes;
   li.fn = step_fn(pl.r, pl.tile, grad);
-  configure_kernel(li.fn, li.smem);
-  int nb = 0;
   li.threads = (kTiles[pl.tile].warps + 1) * 32;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, li.fn, li.threads, li.smem));
+  li.smem = launch_smem(pl, pl.tile, L, stages, li.fn, li.threads);
+  const int nb = occupancy(pl, pl.tile, li.fn, li.threads, li.smem);
   li.grid = std::max(1, std::min(nunits, std::max(nb, 1) * device_sms(pl.device)));
   li.stage_bytes = L.bytes;
   li.off_p = L.off_p;
@@ -1788,7 +1835,8 @@ static void plan_autotune(Plan& pl, int steps) {
       if (c->ny > 1) all2d = false;
       nxmax = std::max(nxmax, c->nx);
     }
-    std::vector<int> tiles = all2d ? std::vector<int>{3} : std::vector<int>{0, 1, 2, 4, 5, 6};
+    std::vector<int> tiles =
+        all2d ? std::vector<int>{3} : std::vector<int>{0, 1, 2, 4, 5, 6, 7, 8};
     std::vector<int> lxs = {16, 32, 48, 64, 80, 96, 128, nxmax};
     cudaStream_t s = pl.cap;
     cudaEvent_t e0, e1;

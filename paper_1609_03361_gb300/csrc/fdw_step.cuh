@@ -27,11 +27,19 @@
 //  - after the chunk, the consumers add the injected values into the nodes the
 //    unit owns (deterministic order, no atomics: no other CTA reads u^{n+1}
 //    during this step) and record the sampled points of u^n.
+// With TQ the x queue lives in tensor memory instead of registers: each
+// thread owns one TMEM lane, where a ring of 2r+1 planes (four values each) is
+// stored twice over, so that the 2r planes x-r .. x+r-1 around the plane being
+// updated are always 8r consecutive columns, read with one load per plane.
+// A plane is written once (two 16-byte stores) when it arrives, and nothing
+// shifts: the register queue costs 2r moves per point and plane, and 2r+1
+// live registers per point.
 #pragma once
 
 #include <cstdio>
 
 #include "fdw_device.cuh"
+#include "fdw_internal.h"
 
 namespace fdw {
 
@@ -86,6 +94,16 @@ __device__ __forceinline__ bool wait_or_abort(uint32_t bar, uint32_t parity, vol
   }
 }
 
+
+// Consumer waits of a warp that uses tensor memory: the warp-collective
+// tcgen05 instructions need every lane to take the same path, so a wait that
+// gave up in any lane counts as given up in all.
+template <bool UNIFORM>
+__device__ __forceinline__ bool cwait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  const bool ok = wait_or_abort(bar, parity, abort);
+  if constexpr (UNIFORM) return __all_sync(0xffffffffu, ok);
+  return ok;
+}
 
 // Model values are stored as s = 1/m (squared velocity) in one of three types.
 template <typename MT>
@@ -146,14 +164,15 @@ __device__ __forceinline__ void dbg_check(const char* what, float got, const flo
 // length 2R+1 so that the queue slots rotate; otherwise the queue shifts by one
 // slot per plane (smaller code).  SPLIT: the per-plane tiles come from the
 // second ring (cursor cc).  Returns false if a wait gave up.
-template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT, typename MT>
+template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT, bool TQ, typename MT>
 __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, const ShotDesc* d,
                                          int u, const unsigned char* smem, uint32_t full0,
                                          uint32_t empty0, Cursor& ca, Cursor& cb,
                                          const unsigned char* csmem, uint32_t cfull0,
                                          uint32_t cempty0, Cursor& cc,
                                          volatile int* abort_flag, int lane, const Lanes L,
-                                         float& tmax) {
+                                         float& tmax, uint32_t tq) {
+  static_assert(!TQ || (NY == 1 && !XU), "the tensor-memory queue holds one row per thread");
   constexpr int TZ = kTZ;
   constexpr int R4 = Halo<R>::R4;
   constexpr int ZW = Halo<R>::ZW;
@@ -188,17 +207,25 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
 
   // x queue of centre values: slot (p - x0 + R) mod Q holds plane p (XU), or
   // slot i holds plane x - R + i (shift)
-  float qv[NY][kVZ][Q];
+  // (with TQ: the ring slot of plane p is (p - x0 + R) mod Q, columns
+  // 4 slot and 4 (slot + Q) of the thread's lane from tq)
+  float qv[NY][kVZ][TQ ? 1 : Q];
+  if constexpr (TQ) tmem_wait_st();  // the previous unit's last stores are done
   bool ok = true;
 #pragma unroll
   for (int i = 0; i < 2 * R; ++i) {
-    if (ok) ok = wait_or_abort(full0 + 8 * ca.stage, ca.phase, abort_flag);
+    if (ok) ok = cwait<TQ>(full0 + 8 * ca.stage, ca.phase, abort_flag);
     const float* U = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes);
 #pragma unroll
     for (int j = 0; j < NY; ++j) {
       const float4 cv = ok ? lds4(U + (r0 + j + R) * ZW + R4 + zl) : make_float4(0.f, 0.f, 0.f, 0.f);
+      if constexpr (TQ) {
+        tmem_st4(tq + 4 * i, cv);
+        tmem_st4(tq + 4 * (i + Q), cv);
+      } else {
 #pragma unroll
-      for (int v = 0; v < kVZ; ++v) qv[j][v][i] = pick(cv, v);
+        for (int v = 0; v < kVZ; ++v) qv[j][v][i] = pick(cv, v);
+      }
 #ifdef FDW_DEBUG_VERIFY
       dbg_check("warm", cv.x, d->u, (long long)P.cur * d->uslot, un.x0 - R + i, un.y0 + r0 + j,
                 z, d->nx, ny, nz, nzp, u);
@@ -215,6 +242,8 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
   float* acc = d->acc;
   const float* eta_x = d->eta;
   float ex_next = etaf ? 0.f : eta_x[un.x0];  // x part of the damping, one plane ahead
+  int tq_sl = 0;  // ring slot of plane x - R (TQ)
+  (void)tq_sl;
 #pragma unroll 1
   for (int xb = un.x0; xb < un.x1; xb += XS) {
 #pragma unroll
@@ -222,20 +251,45 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
       const int t = XU ? t0 : 0;
       const int x = xb + t0;
       if (x >= un.x1) break;
+      // TQ: planes x-R .. x+R-1 come from the tensor-memory ring; the window
+      // starts at the slot of plane x-R, and its load is in flight while the
+      // warp waits for the halo planes and reads them
+      TmemWindow<TQ ? R : 1> win;
+      (void)win;
+      if constexpr (TQ) {
+        tmem_wait_st();  // the previous plane's ring stores are done
+        win.issue(tq + 4 * tq_sl);
+      }
       // centre values of plane x+R join the queue
-      if (!wait_or_abort(full0 + 8 * ca.stage, ca.phase, abort_flag)) return false;
+      if (!cwait<TQ>(full0 + 8 * ca.stage, ca.phase, abort_flag)) {
+        if constexpr (TQ) win.wait();
+        return false;
+      }
+      float4 ahead[NY];
+      (void)ahead;
       {
         const float* Ua = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes);
 #pragma unroll
         for (int j = 0; j < NY; ++j) {
           const float4 cv = lds4(Ua + (r0 + j + R) * ZW + R4 + zl);
+          if constexpr (TQ) {
+            ahead[j] = cv;
+          } else {
 #pragma unroll
-          for (int v = 0; v < kVZ; ++v) qv[j][v][(t + 2 * R) % Q] = pick(cv, v);
+            for (int v = 0; v < kVZ; ++v) qv[j][v][(t + 2 * R) % Q] = pick(cv, v);
+          }
 #ifdef FDW_DEBUG_VERIFY
           dbg_check("ahead", cv.x, d->u, (long long)P.cur * d->uslot, x + R, un.y0 + r0 + j, z,
                     d->nx, ny, nz, nzp, u);
 #endif
         }
+      }
+      if constexpr (TQ) {
+        // plane x+R takes the slot of plane x-R-1, outside the window in flight
+        const int sa = tq_sl == 0 ? Q - 1 : tq_sl - 1;
+        tmem_st4(tq + 4 * sa, ahead[0]);
+        tmem_st4(tq + 4 * (sa + Q), ahead[0]);
+        tq_sl = tq_sl + 1 == Q ? 0 : tq_sl + 1;
       }
       // a look-ahead plane past the chunk is only needed for its centre
       // values; it is handed back after the update below has consumed them
@@ -247,7 +301,10 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
       const float* U = reinterpret_cast<const float*>(sb);
       const unsigned char* tb = sb;  // the plane's own tiles
       if (SPLIT) {
-        if (!wait_or_abort(cfull0 + 8 * cc.stage, cc.phase, abort_flag)) return false;
+        if (!cwait<TQ>(cfull0 + 8 * cc.stage, cc.phase, abort_flag)) {
+          if constexpr (TQ) win.wait();
+          return false;
+        }
         tb = csmem + cc.stage * P.cstage_bytes;
       }
       const float ex = ex_next;
@@ -274,6 +331,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
 #pragma unroll
         for (int j = 0; j < NY; ++j) yr[R + j] = lds4(U + (r0 + j + R) * ZW + R4 + zl);
       }
+      if constexpr (TQ) win.wait();
 #pragma unroll
       for (int j = 0; j < NY; ++j) {
         float wz[NW];
@@ -297,7 +355,12 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
           float lx = 0.f, ly = 0.f, lz = 0.f;
 #pragma unroll
           for (int k = 1; k <= R; ++k) {
-            lx = fmaf(P.w[0][k], qv[j][v][(t + R - k) % Q] + qv[j][v][(t + R + k) % Q], lx);
+            if constexpr (TQ) {
+              const float xb = k < R ? win.v(4 * (R + k) + v) : pick(ahead[j], v);
+              lx = fmaf(P.w[0][k], win.v(4 * (R - k) + v) + xb, lx);
+            } else {
+              lx = fmaf(P.w[0][k], qv[j][v][(t + R - k) % Q] + qv[j][v][(t + R + k) % Q], lx);
+            }
             ly = fmaf(P.w[1][k], pick(yr[R + j - k], v) + pick(yr[R + j + k], v), ly);
             lz = fmaf(P.w[2][k], wz[R4 + v - k] + wz[R4 + v + k], lz);
           }
@@ -346,7 +409,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
           }
         }
       }
-      if (!XU) {
+      if (!XU && !TQ) {
 #pragma unroll
         for (int j = 0; j < NY; ++j)
 #pragma unroll
@@ -364,9 +427,10 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
 // resident CTAs per SM (136 registers a thread), which its smaller shared
 // memory allows; every other instance leaves the register count to the
 // compiler (a minimum of 0 blocks states no constraint).
-template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT = GRAD>
-__global__ void __launch_bounds__((BY + 1) * 32, (SPLIT && !GRAD && R >= 7) ? 3 : 0)
+template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT = GRAD, bool TQ = false>
+__global__ void __launch_bounds__((BY + 1) * 32, (SPLIT && !GRAD && R >= 7 && !TQ) ? 3 : 0)
 step_kernel(const __grid_constant__ StepParams P) {
+  static_assert(!TQ || BY == 4, "the tensor-memory queue maps the four consumer warps to the four lane quarters");
   constexpr int TZ = kTZ;
   constexpr int TY = 4 * BY * NY;
   constexpr int R4 = Halo<R>::R4;
@@ -397,6 +461,15 @@ step_kernel(const __grid_constant__ StepParams P) {
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  // tensor-memory ring of the x queue (TQ): allocated by warp 0, freed by it
+  // at the end; each consumer warp w uses lanes 32 w .. 32 w + 31
+  __shared__ uint32_t s_tmem;
+  if constexpr (TQ) {
+    if (warp == 0) {
+      tmem_alloc(smem_u32(&s_tmem), (uint32_t)tq_columns(R));
+      tmem_fence_before_sync();
+    }
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(full0 + 8 * s, 1);
@@ -413,6 +486,11 @@ step_kernel(const __grid_constant__ StepParams P) {
     fence_barrier_init();
   }
   __syncthreads();
+  uint32_t tq = 0;
+  if constexpr (TQ) {
+    tmem_fence_after_sync();
+    tq = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+  }
 
   if (warp == BY) {
     // ------------------------------ producer ------------------------------
@@ -513,7 +591,7 @@ step_kernel(const __grid_constant__ StepParams P) {
     bool ok = true;
     while (true) {
       // the stage of the next unit's first plane names the unit
-      if (!wait_or_abort(full0 + 8 * ca.stage, ca.phase, abort_flag)) {
+      if (!cwait<TQ>(full0 + 8 * ca.stage, ca.phase, abort_flag)) {
         ok = false;
         break;
       }
@@ -523,19 +601,19 @@ step_kernel(const __grid_constant__ StepParams P) {
       const ShotDesc* d = P.shots + un.shot;
       const int mtype = d->mtype;
       if (mtype == kF16)
-        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, __half>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
-                                               abort_flag, lane, L, tmax);
+        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, __half>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
+                                               abort_flag, lane, L, tmax, tq);
       else if (mtype == kBF16)
-        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, __nv_bfloat16>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
-                                                      abort_flag, lane, L, tmax);
+        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, __nv_bfloat16>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
+                                                      abort_flag, lane, L, tmax, tq);
       else
-        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, float>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
-                                              abort_flag, lane, L, tmax);
+        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, float>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
+                                              abort_flag, lane, L, tmax, tq);
       if (!ok) break;
 
       // ---- unit tail: injection into u^{n+1} and sampling of u^n ----
       mbar_arrive(tail);
-      if (!wait_or_abort(tail, tail_phase, abort_flag)) { ok = false; break; }
+      if (!cwait<TQ>(tail, tail_phase, abort_flag)) { ok = false; break; }
       tail_phase ^= 1u;
       const int nx = d->nx, ny = d->ny, nzp = d->nzp;
       const bool etaf = (P.flags & kEtaField) != 0;
@@ -632,6 +710,10 @@ step_kernel(const __grid_constant__ StepParams P) {
       atomicOr(P.err, kErrTimeoutFull);
       *abort_flag = 1;
     }
+    if constexpr (TQ) {  // the warp's last ring stores are done before the ring is freed
+      tmem_wait_st();
+      tmem_fence_before_sync();
+    }
   }
   __syncthreads();
   // On an aborted launch, wait (bounded) for the loads still in flight before
@@ -654,6 +736,12 @@ step_kernel(const __grid_constant__ StepParams P) {
         while (!mbar_try_wait(cfull0 + 8 * st, ph) && clock64() - t0 < kWaitBudget) {
         }
       }
+    }
+  }
+  if constexpr (TQ) {
+    if (warp == 0) {
+      tmem_fence_after_sync();
+      tmem_dealloc(s_tmem, (uint32_t)tq_columns(R));
     }
   }
 }

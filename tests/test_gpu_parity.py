@@ -43,9 +43,24 @@ def test_forward_3d_all_orders(fw, p):
     assert_close(u, uref, TOL, "wavefield")
 
 
+@pytest.mark.parametrize("p", [2, 4, 6, 8, 10, 12, 14, 16])
+@pytest.mark.parametrize("tile", [7, 8])
+def test_forward_3d_tensor_memory_queue_all_orders(fw, p, tile):
+    """Tiles 7 and 8 keep the x queue in tensor memory: the same arithmetic as
+    tiles 4 and 6, so bit for bit their results, and the oracle's to 1e-4."""
+    pb = Problem((37, 45, 29), 10.0, p, 8, 70, nsrc=2, nrec=9, seed=p)
+    rec, u = _fwd(fw, pb, tiling=(tile, 0, 0))
+    ref, uref = pb.oracle_forward(final=True)
+    assert_close(rec, ref, TOL, "traces")
+    assert_close(u, uref, TOL, "wavefield")
+    rec4, u4 = _fwd(fw, pb, tiling=(tile - 3 if tile == 7 else 6, 0, 0))
+    assert np.array_equal(rec, rec4) and np.array_equal(u, u4)
+
+
 @pytest.mark.parametrize("tiling", [(0, 0, 0), (1, 0, 0), (2, 0, 0), (4, 0, 0), (5, 0, 0),
                                     (0, 5, 0), (2, 3, 6), (1, 13, 0), (4, 64, 7), (0, 1, 0),
-                                    (5, 7, 9), (6, 0, 0), (6, 9, 10)])
+                                    (5, 7, 9), (6, 0, 0), (6, 9, 10), (7, 0, 0), (7, 1, 6),
+                                    (7, 13, 9), (8, 0, 0), (8, 9, 10)])
 def test_forward_3d_tilings(fw, tiling):
     pb = Problem((40, 51, 35), 12.5, 8, 6, 60, nsrc=3, nrec=12, seed=11)
     rec, u = _fwd(fw, pb, tiling=tiling)
@@ -58,7 +73,8 @@ def test_tilings_agree_bitwise(fw):
     """Every tiling computes each point with the same arithmetic."""
     pb = Problem((30, 33, 41), 10.0, 8, 5, 50, nsrc=2, nrec=8, seed=5)
     base_rec, base_u = _fwd(fw, pb, tiling=(0, 0, 0))
-    for t in [(1, 0, 0), (2, 7, 0), (0, 2, 6), (1, 64, 9), (4, 3, 0), (5, 11, 7), (6, 13, 8)]:
+    for t in [(1, 0, 0), (2, 7, 0), (0, 2, 6), (1, 64, 9), (4, 3, 0), (5, 11, 7), (6, 13, 8),
+              (7, 0, 0), (7, 5, 6), (8, 13, 8)]:
         rec, u = _fwd(fw, pb, tiling=t)
         assert np.array_equal(rec, base_rec), t
         assert np.array_equal(u, base_u), t
@@ -126,13 +142,14 @@ def test_degenerate_cases(fw):
     assert rec.shape == (1, 3) and np.count_nonzero(rec) == 0
 
 
-@pytest.mark.parametrize("ndim,p", [(3, 4), (3, 8), (3, 16), (2, 8)])
-def test_adjoint_parity_and_dot_test(fw, ndim, p):
+@pytest.mark.parametrize("ndim,p,tiling", [(3, 4, None), (3, 8, None), (3, 16, None), (2, 8, None),
+                                           (3, 8, (7, 0, 0)), (3, 16, (8, 0, 0))])
+def test_adjoint_parity_and_dot_test(fw, ndim, p, tiling):
     shape = (31, 27, 35) if ndim == 3 else (50, 45)
     pb = Problem(shape, 10.0, p, 6, 70, nsrc=2, nrec=7, seed=21 + p)
     rng = np.random.default_rng(p)
     d = rng.standard_normal((pb.nt, 7)).astype(np.float32)
-    s = pb.solver(fw)
+    s = pb.solver(fw, tiling=tiling)
     qa = s.adjoint(d)
     Fq = s.forward(pb.q32)
     s.sync()
@@ -144,12 +161,13 @@ def test_adjoint_parity_and_dot_test(fw, ndim, p):
     assert abs(a - b) / abs(a) < 1e-5
 
 
-@pytest.mark.parametrize("k", [1, 4, 9, 70])
-def test_gradient_fp32_checkpoints(fw, k):
+@pytest.mark.parametrize("k,tiling", [(1, None), (4, None), (9, None), (70, None), (4, (7, 0, 0)),
+                                      (9, (8, 11, 0))])
+def test_gradient_fp32_checkpoints(fw, k, tiling):
     pb = Problem((29, 26, 31), 10.0, 8, 6, 70, nsrc=1, nrec=8, seed=31)
     rng = np.random.default_rng(3)
     resid = rng.standard_normal((pb.nt, 8)).astype(np.float32)
-    s = pb.solver(fw)
+    s = pb.solver(fw, tiling=tiling)
     s.forward_ckpt(pb.q32, k, "f32")
     g = s.gradient(resid)
     s.sync()
@@ -256,7 +274,7 @@ def test_autotune_keeps_results(fw):
     s = pb.solver(fw)
     s.autotune(3)
     t = s.tiling()
-    assert t["tile"] in (0, 1, 2, 4, 5, 6) and t["stages"] >= 6
+    assert t["tile"] in (0, 1, 2, 4, 5, 6, 7, 8) and t["stages"] >= 6
     rec = s.forward(pb.q32)
     s.sync()
     s.close()
@@ -306,7 +324,7 @@ def full_grid_case():
 
 # the autotuner's choice (as in the bench) and the tilings the bench's tuner
 # has picked on the GB300 (tile 4 with x chunks of 80 and 64, 7 stages)
-@pytest.mark.parametrize("tiling", [None, (4, 80, 7), (4, 64, 7)])
+@pytest.mark.parametrize("tiling", [None, (4, 80, 7), (4, 64, 7), (7, 80, 7)])
 def test_config_3d_256_so8_full_grid_first_steps(fw, full_grid_case, tiling):
     w, q32, ref, uref = full_grid_case
     dev = torch.device("cuda", 0)
