@@ -85,7 +85,13 @@ __device__ __forceinline__ bool tb_unit(const TbParams& P, const Unit& un, const
   constexpr int Q = 2 * R + 1;       // x queue length
   constexpr int EPL = EY * kTbEZ;    // floats of one region-E plane
   constexpr int NCT = EY * 16;       // consumer threads
-  constexpr int NT2 = TY * kTbQ;     // second-step threads: one output quad each
+  // second-step threads: one output quad each, 16 threads per output row (the
+  // last 16 - kTbQ of them idle), so that the eight threads of a 16-byte
+  // shared-memory access phase read eight consecutive quads of one row: no
+  // bank conflicts whatever the row pitch (with rows of kTbQ threads back to
+  // back, a phase straddled two rows whose pitches map to the same banks)
+  constexpr int NT2 = TY * 16;
+  static_assert(NT2 <= NCT, "second-step threads");
   constexpr bool F32 = sizeof(MT) == 4;
   const int S = P.stages;
   const int nx = d->nx, ny = d->ny, nz = d->nz, nzp = d->nzp;
@@ -115,8 +121,8 @@ __device__ __forceinline__ bool tb_unit(const TbParams& P, const Unit& un, const
   const int soff = F32 ? eoff : ry * kTbHZ + 4 + 4 * qz;
 
   // second step: output quad (ty, tq) of the tile, threads below NT2
-  const bool two = tid < NT2;
-  const int ty = tid / kTbQ, tq = tid - ty * kTbQ;
+  const int ty = tid >> 4, tq = tid & 15;
+  const bool two = tid < NT2 && tq < kTbQ;
   const int y2 = un.y0 + ty, z2 = un.z0 + 4 * tq;
   const bool own2 = two && y2 < ny && z2 < nz;
   bool zin2[4];

@@ -29,7 +29,9 @@ constexpr int kTbMaxR = 2;           // largest radius with a two-step kernel
 // 8 consumer warps and a producer warp, two CTAs per SM) or 34 / 32 (variant
 // 1: 17 or 16 consumer warps, one CTA per SM); the output tile has TY = EY - 2r
 // rows.  The first step gives each consumer thread one quad of region E, the
-// second step one quad of the output tile (TY x 14 threads).
+// second step one quad of the output tile (16 threads per output row, the
+// last two idle, so that a row's shared-memory reads are free of bank
+// conflicts).
 constexpr int kTbVariants = 2;
 
 constexpr int tb_ey(int r, int variant) {
