@@ -220,7 +220,8 @@ fdw_status fdw_set_checkpoint_budget(fdw_ctx* ctx, int max_pairs);
 int fdw_checkpoint_schedule(int nseg, int nslots, int* actions, int cap);
 
 /* Force a tile configuration: tile index (0..8, -1 = default; 3 is meant for
- * 2D grids, 6 keeps per-plane tiles in a second ring), x-chunk length (0 = default) and pipeline depth of the forward
+ * 2D grids, 6 keeps per-plane tiles in a second ring, 7 and 8 are 4 and 6
+ * with the x-direction queue in tensor memory), x-chunk length (0 = default) and pipeline depth of the forward
  * and adjoint steps (>= r + 2 with r = space_order / 2, 0 = default; the
  * gradient step picks its own).  FDW_ERR_ARG outside these ranges. */
 fdw_status fdw_set_tiling(fdw_ctx* ctx, int tile, int xchunk, int stages);

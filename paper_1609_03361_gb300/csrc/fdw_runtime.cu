@@ -150,6 +150,7 @@ struct fdw_ctx {
   int mtype = kF32;
   bool model_set = false;
   float* eta = nullptr;         // eta*dt/2 profiles [nx + ny + nz]
+  std::vector<float> eta_host;  // the same profiles on the host
   float* etaf = nullptr;        // eta*dt/2 field (pitched)
   bool use_etaf = false;
   PointSet src, rec;
@@ -551,6 +552,20 @@ static void upload_vec(void** dptr, const void* src, size_t bytes) {
   if (bytes) CK(cudaMemcpy(*dptr, src, bytes, cudaMemcpyHostToDevice));
 }
 
+// True when the built-in damping is zero at every grid point of the unit (the
+// step kernel then skips the damping terms there).
+static bool undamped(const fdw_ctx* c, const Unit& u, int TY) {
+  if (c->use_etaf) return false;
+  const std::vector<float>& e = c->eta_host;
+  for (int x = u.x0; x < u.x1; ++x)
+    if (e[x] != 0.f) return false;
+  for (int y = u.y0; y < std::min(u.y0 + TY, c->ny); ++y)
+    if (e[c->nx + y] != 0.f) return false;
+  for (int z = u.z0; z < std::min(u.z0 + kTZ, c->nz); ++z)
+    if (e[c->nx + c->ny + z] != 0.f) return false;
+  return true;
+}
+
 // Units and the per-unit injection / sampling lists of each role.
 static void build_lists(Plan& pl) {
   pl.release_lists();
@@ -630,7 +645,9 @@ static void build_lists(Plan& pl) {
     for (size_t q = 0; q < order.size(); ++q) {
       const int li = order[q];
       pos[ri][li] = (int)q;
-      pl.units.push_back(make_unit(r.shot, r.x0, r.x1, li, ck, TY));
+      Unit un = make_unit(r.shot, r.x0, r.x1, li, ck, TY);
+      if (undamped(pl.shots[r.shot], un, TY)) un.flags |= kUnitUndamped;
+      pl.units.push_back(un);
     }
   }
   const int U = (int)pl.units.size();
@@ -2042,6 +2059,7 @@ static fdw_status create_ctx(fdw_ctx** out, int ndim, const int64_t* shape, cons
     }
     c->eta = dalloc<float>(prof.size());
     CK(cudaMemcpy(c->eta, prof.data(), prof.size() * sizeof(float), cudaMemcpyHostToDevice));
+    c->eta_host = prof;
   });
   if (st != FDW_OK) return st;
   *out = c.release();

@@ -164,7 +164,8 @@ __device__ __forceinline__ void dbg_check(const char* what, float got, const flo
 // length 2R+1 so that the queue slots rotate; otherwise the queue shifts by one
 // slot per plane (smaller code).  SPLIT: the per-plane tiles come from the
 // second ring (cursor cc).  Returns false if a wait gave up.
-template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT, bool TQ, typename MT>
+template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT, bool TQ, typename MT,
+          bool DAMP = true>
 __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, const ShotDesc* d,
                                          int u, const unsigned char* smem, uint32_t full0,
                                          uint32_t empty0, Cursor& ca, Cursor& cb,
@@ -308,7 +309,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
         tb = csmem + cc.stage * P.cstage_bytes;
       }
       const float ex = ex_next;
-      if (!etaf && x + 1 < un.x1) ex_next = eta_x[x + 1];
+      if (DAMP && !etaf && x + 1 < un.x1) ex_next = eta_x[x + 1];
       const float* Pp = reinterpret_cast<const float*>(tb + P.off_p);
       const long long xoff = (long long)x * plane;
       // y neighbours of the thread's rows: local rows r0-R .. r0+NY-1+R
@@ -365,11 +366,15 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
             lz = fmaf(P.w[2][k], wz[R4 + v - k] + wz[R4 + v + k], lz);
           }
           const float lap = fmaf(P.csum, c, lx + ly + lz);
-          const float sm = pick(sv, v), e = pick(ev, v), prev = pick(pv, v);
-          const float es = e * sm;
-          // [2u - (1 - e s) u- + s dt^2 L u] / (1 + e s): the three-level update divided by m
-          const float num = fmaf(es, prev, fmaf(sm, lap, 2.f * c) - prev);
-          val[j][v] = __fdividef(num, 1.f + es);
+          const float sm = pick(sv, v), prev = pick(pv, v);
+          if constexpr (DAMP) {
+            const float es = pick(ev, v) * sm;
+            // [2u - (1 - e s) u- + s dt^2 L u] / (1 + e s): the three-level update divided by m
+            const float num = fmaf(es, prev, fmaf(sm, lap, 2.f * c) - prev);
+            val[j][v] = __fdividef(num, 1.f + es);
+          } else {  // e = 0 at every point of the unit: 2u - u- + s dt^2 L u
+            val[j][v] = fmaf(sm, lap, 2.f * c) - prev;
+          }
           if (GRAD) d2t[j][v] = val[j][v] - 2.f * c + prev;  // second time difference of lambda
         }
         if (GRAD) {
@@ -606,6 +611,9 @@ step_kernel(const __grid_constant__ StepParams P) {
       else if (mtype == kBF16)
         ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, __nv_bfloat16>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
                                                       abort_flag, lane, L, tmax, tq);
+      else if (!XU && (un.flags & kUnitUndamped))  // every point of the unit undamped
+        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, float, false>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
+                                                     abort_flag, lane, L, tmax, tq);
       else
         ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, float>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
                                               abort_flag, lane, L, tmax, tq);

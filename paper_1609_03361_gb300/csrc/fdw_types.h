@@ -65,8 +65,11 @@ struct Unit {
   int shot;
   int x0, x1;
   int y0, z0;
-  int pad[3];
+  int flags;           // kUnitUndamped: eta = 0 at every grid point of the unit
+  int pad[2];
 };
+
+enum UnitFlags : int { kUnitUndamped = 1 };
 
 // One grid node that receives an injected value, and the range of its terms.
 struct InjNode {
