@@ -39,7 +39,8 @@ B_ALG = 16  # algorithmic bytes per point update: read u^n, u^{n-1}, m; write u^
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
 KERNEL_SOURCES = ["paper_1609_03361_gb300/csrc/fdw_step.cuh",
                   "paper_1609_03361_gb300/csrc/fdw_device.cuh",
-                  "paper_1609_03361_gb300/csrc/fdw_types.h"]
+                  "paper_1609_03361_gb300/csrc/fdw_types.h",
+                  "paper_1609_03361_gb300/csrc/fdw_internal.h"]
 
 
 def kernel_hash():
@@ -282,24 +283,29 @@ def run_forward(args, world, rank, local):
     s.sync()
     updates = pts * (w.nt - 1)
     value = world * updates * args.steps / (ms * 1e-3) / 1e9
-    launches = args.steps * w.nt   # (nt-1) step kernels + 1 sampling kernel per forward
+    # one persistent step-kernel launch over the nt-1 steps and one sampling
+    # launch for the last time sample, per forward run
+    launches = args.steps * 2
 
-    # roofline of the step kernel (its launches fill the timed region)
-    avg_launch_s = (ms_local * 1e-3) / (args.steps * (w.nt - 1))
-    achieved = B_ALG * pts / avg_launch_s / 1e9
+    # roofline of the step kernel (its launches fill the timed region),
+    # per time step of the persistent launch: 16 B x points per step over
+    # the launch's time per step
+    avg_step_s = (ms_local * 1e-3) / (args.steps * (w.nt - 1))
+    achieved = B_ALG * pts / avg_step_s / 1e9
     peak, peak_kind = measured_peaks()
     traffic = None
     try:
         with open(PROFILE_TRAFFIC) as f:
             tr = json.load(f)
         if tr.get("kernel_hash") == kernel_hash() and tr.get("points") == pts:
-            traffic = tr["dram_bytes_per_launch"]
+            traffic = tr["dram_bytes_per_step"]
     except Exception:
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "frac_of_nominal_7900": achieved / 7900.0,
-                "bytes_per_point": B_ALG, "points_per_launch": pts}
+                "bytes_per_point": B_ALG, "points_per_step": pts,
+                "per": "time step of the persistent step-kernel launch (nt - 1 steps a launch)"}
 
     # end to end through the public API with pinned host buffers
     e2e = None

@@ -178,6 +178,9 @@ struct fdw_ctx {
 
   // tiling override
   int tile = -1, xchunk = 0, stages = 0;
+  // plain forward passes run as one persistent launch over all time steps
+  // (slabs step one launch at a time)
+  bool persist = true;
 
   // staging buffers for host arrays
   std::map<int, std::pair<void*, size_t>> staging;
@@ -217,6 +220,12 @@ struct Plan {
   int tile_req = -1, lx_req = 0, stages_req = 0;
   std::vector<Unit> units;
   Unit* d_units = nullptr;
+  // rows of units (one x chunk of one shot with all its column tiles): the
+  // rows a row's units read, units per row, finished units per row
+  int nrows = 0;
+  int2* d_row_deps = nullptr;
+  int* d_row_units = nullptr;
+  int* d_row_done = nullptr;
   RoleLists lists[kNumRoles];
   std::vector<ShotDesc> hdesc[kNumRoles];
   ShotDesc* d_desc[kNumRoles] = {nullptr, nullptr, nullptr};
@@ -239,6 +248,7 @@ struct Plan {
     int grid, threads, stages, cstages, cstage_bytes;
     size_t smem;
     int stage_bytes, off_p, off_m, off_f, off_a, off_e;
+    int resident;  // CTAs that fit on the device at once
   };
   std::map<std::tuple<int, int, int, int, int, int>, LaunchInfo> launch_cache;
   std::vector<double> weights;       // unscaled second-derivative weights c_0..c_r
@@ -292,7 +302,14 @@ struct Plan {
   void release_lists() {
     for (auto& l : lists) l.release();
     dfree(d_units);
+    dfree(d_row_deps);
+    dfree(d_row_units);
+    dfree(d_row_done);
     d_units = nullptr;
+    d_row_deps = nullptr;
+    d_row_units = nullptr;
+    d_row_done = nullptr;
+    nrows = 0;
   }
   ~Plan() {
     clear_graphs();
@@ -647,8 +664,26 @@ static void build_lists(Plan& pl) {
       pos[ri][li] = (int)q;
       Unit un = make_unit(r.shot, r.x0, r.x1, li, ck, TY);
       if (undamped(pl.shots[r.shot], un, TY)) un.flags |= kUnitUndamped;
+      un.row = (int)ri;
       pl.units.push_back(un);
     }
+  }
+  {
+    // a row's units read the planes x0 - r .. x1 + r - 1 of their shot: the
+    // rows holding them are consecutive in the table
+    std::vector<int2> deps(fine.size());
+    std::vector<int> nu(fine.size());
+    for (size_t ri = 0; ri < fine.size(); ++ri) {
+      const Row& r = fine[ri];
+      const fdw_ctx* c = pl.shots[r.shot];
+      const int xa = std::max(r.x0 - pl.r, c->own0), xb = std::min(r.x1 + pl.r, c->own1) - 1;
+      deps[ri] = make_int2(xrow[r.shot][xa], xrow[r.shot][xb]);
+      nu[ri] = cols[r.shot][0] * cols[r.shot][1];
+    }
+    pl.nrows = (int)fine.size();
+    upload_vec((void**)&pl.d_row_deps, deps.data(), deps.size() * sizeof(int2));
+    upload_vec((void**)&pl.d_row_units, nu.data(), nu.size() * sizeof(int));
+    pl.d_row_done = dalloc<int>(fine.size());
   }
   const int U = (int)pl.units.size();
   // unit of a node, -1 for a plane no unit updates (a slab's ghost planes)
@@ -878,6 +913,7 @@ struct StepArgs {
   int flags;
   bool grad;
   int amax_slot = 0;
+  int step0 = 0, step_end = 1;  // kPersist: the steps of the launch
 };
 
 static const Plan::LaunchInfo& launch_info(Plan& pl, bool grad) {
@@ -897,6 +933,7 @@ static const Plan::LaunchInfo& launch_info(Plan& pl, bool grad) {
   li.threads = (kTiles[pl.tile].warps + 1) * 32;
   li.smem = launch_smem(pl, pl.tile, L, stages, li.fn, li.threads);
   const int nb = occupancy(pl, pl.tile, li.fn, li.threads, li.smem);
+  li.resident = std::max(nb, 1) * device_sms(pl.device);
   li.grid = std::max(1, std::min(nunits, std::max(nb, 1) * device_sms(pl.device)));
   li.stage_bytes = L.bytes;
   li.off_p = L.off_p;
@@ -988,10 +1025,18 @@ static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s) {
   P.off_e = li.off_e;
   stencil_weights(pl, P.w, &P.csum, &P.dt2);
   P.err = pl.d_err;
+  const bool persist = (a.flags & kPersist) != 0;
+  P.step0 = a.step0;
+  P.step_end = a.step_end;
+  P.row_done = pl.d_row_done;
+  P.row_deps = pl.d_row_deps;
+  P.row_units = pl.d_row_units;
 
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof(cfg));
-  cfg.gridDim = dim3(li.grid);
+  // a persistent launch has (step_end - step0) x nunits tickets: every CTA
+  // that fits takes part
+  cfg.gridDim = dim3(persist ? (unsigned)li.resident : (unsigned)li.grid);
   cfg.blockDim = dim3(li.threads);
   cfg.dynamicSmemBytes = li.smem;
   cfg.stream = s;
@@ -1029,6 +1074,14 @@ static void run_graph(Plan& pl, const std::string& key, cudaStream_t s, F&& body
 
 // ---------------------------------------------------------------- passes
 
+// Plain forward passes of a plan run as one persistent launch when every
+// shot asks for it (fdw_set_persistent) and none is a slab.
+static bool plan_persistent(const Plan& pl) {
+  for (auto* c : pl.shots)
+    if (!c->persist || c->slab) return false;
+  return true;
+}
+
 // Forward time loop over all shots of a plan; snapshots every k steps if k > 0.
 static void forward_body(Plan& pl, int k, int stype, cudaStream_t s) {
   const int nt = pl.shots[0]->nt;
@@ -1062,6 +1115,21 @@ static void forward_body(Plan& pl, int k, int stype, cudaStream_t s) {
     last_start = (pl.rv_nseg - 1) * k;
     if (last_start == 0)
       for (auto* c : pl.shots) CK(cudaMemsetAsync(c->seg, 0, sizeof(float) * 2 * c->slot, s));
+  }
+  if (k == 0 && plan_persistent(pl)) {
+    // plain forward: every step in one launch, units of step n + 1 starting
+    // as soon as the rows they read have finished step n
+    CK(cudaMemsetAsync(pl.d_row_done, 0, sizeof(int) * pl.nrows, s));
+    if (nt > 1) {
+      StepArgs a{kRoleFwd, 0, 1, 1, 0, 0, 0, flags_base | kPersist, false};
+      a.step0 = 0;
+      a.step_end = nt - 1;
+      launch_step(pl, a, s);
+    }
+    if (pl.max_rec > 0)
+      CK(launch_sample(pl.d_desc[kRoleFwd], (int)pl.shots.size(), pl.max_rec, (nt - 1) & 1, nt - 1,
+                       s));
+    return;
   }
   for (int n = 0; n + 1 < nt; ++n) {
     StepArgs a{kRoleFwd, n & 1, (n + 1) & 1, (n + 1) & 1, 0, n, n, flags_base, false};
@@ -1727,6 +1795,7 @@ static void plan_forward(Plan& pl, const float* const* q, float* const* rec, int
   std::ostringstream key;
   key << "fwd k" << k << " t" << stype << " rv" << (k > 0 && pl.shots[0]->revolve ? pl.shots[0]->nsnap : 0);
   if (tb) key << " tb";
+  if (k == 0 && !tb && plan_persistent(pl)) key << " ps";
   run_graph(pl, key.str(), s, [&](cudaStream_t st) {
     if (tb) tb_forward_body(pl, st);
     else forward_body(pl, k, stype, st);
@@ -1815,7 +1884,7 @@ static std::string tune_key(const Plan& pl) {
   cudaDeviceProp prop;
   CK(cudaGetDeviceProperties(&prop, pl.device));
   std::ostringstream os;
-  os << prop.name << "|r" << pl.r << "|m" << plan_mtype(pl) << "|";
+  os << prop.name << "|r" << pl.r << "|m" << plan_mtype(pl) << "|p" << plan_persistent(pl) << "|";
   for (auto* c : pl.shots) os << c->nx << "x" << c->ny << "x" << c->nz << ";";
   return os.str();
 }
@@ -1883,6 +1952,7 @@ static void plan_autotune(Plan& pl, int steps) {
     if (pl.max_src > 0) flags |= kInject;
     if (pl.max_rec > 0) flags |= kSample;
     // time `n` forward steps of one tiling (after two untimed ones), ms
+    const bool persistent = plan_persistent(pl);
     auto time_config = [&](int t, int lx, int st, int n) {
       pl.tile = t;
       pl.lx = lx;
@@ -1897,12 +1967,25 @@ static void plan_autotune(Plan& pl, int steps) {
       upload_desc(pl, kRoleFwd, s);
       StepArgs a{kRoleFwd, 0, 1, 1, 0, 0, 0, flags, false};
       reset_tickets(pl, s);
-      for (int w = 0; w < 2; ++w) launch_step(pl, a, s);
-      CK(cudaEventRecord(e0, s));
-      for (int i = 0; i < n; ++i) {
-        a.cur = i & 1; a.prev = a.out = (i + 1) & 1;
-        a.inj_row = a.smp_row = i + 2;
+      if (persistent) {
+        // as the plain forward runs: one persistent launch over the steps
+        a.flags |= kPersist;
+        a.step0 = 0;
+        a.step_end = 2;
+        CK(cudaMemsetAsync(pl.d_row_done, 0, sizeof(int) * pl.nrows, s));
         launch_step(pl, a, s);
+        CK(cudaMemsetAsync(pl.d_row_done, 0, sizeof(int) * pl.nrows, s));
+        a.step_end = n;
+        CK(cudaEventRecord(e0, s));
+        launch_step(pl, a, s);
+      } else {
+        for (int w = 0; w < 2; ++w) launch_step(pl, a, s);
+        CK(cudaEventRecord(e0, s));
+        for (int i = 0; i < n; ++i) {
+          a.cur = i & 1; a.prev = a.out = (i + 1) & 1;
+          a.inj_row = a.smp_row = i + 2;
+          launch_step(pl, a, s);
+        }
       }
       CK(cudaEventRecord(e1, s));
       CK(cudaEventSynchronize(e1));
@@ -2386,6 +2469,15 @@ fdw_status fdw_set_tiling(fdw_ctx* c, int tile, int xchunk, int stages) {
     c->xchunk = xchunk;
     c->stages = stages;
     c->plan.reset();
+  });
+}
+
+fdw_status fdw_set_persistent(fdw_ctx* c, int on) {
+  if (!c) return FDW_ERR_ARG;
+  return guard(&c->err, [&] {
+    if (on != 0 && on != 1) fail(FDW_ERR_ARG, "on must be 0 or 1");
+    if (on && c->slab) fail(FDW_ERR_STATE, "a slab context steps one step at a time (fdw_step)");
+    c->persist = on != 0;
   });
 }
 

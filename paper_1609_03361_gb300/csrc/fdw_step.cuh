@@ -141,6 +141,47 @@ struct Lanes {
   int zl;  // local z of the thread's first point (multiple of 4)
 };
 
+// Wavefield slots and time rows of the step a unit belongs to (one step per
+// launch: the launch's; kPersist: the unit's own step n, with u^n in slot
+// n & 1 and u^{n+1} written over u^{n-1} in slot (n + 1) & 1).
+struct StepCtx {
+  int cur, prev, out;
+  int inj_row, smp_row;
+};
+
+__device__ __forceinline__ StepCtx step_ctx(const StepParams& P, int n) {
+  if (P.flags & kPersist) return StepCtx{n & 1, (n + 1) & 1, (n + 1) & 1, n, n};
+  return StepCtx{P.cur, P.prev, P.out, P.inj_row, P.smp_row};
+}
+
+// kPersist: wait (bounded) until every unit of the rows that a unit of `row`
+// reads has finished the launch's step k - 1, then order those units'
+// global writes before this thread's tensor loads.  The counters are read
+// together first; a fence turns the reads that saw the counts into acquires.
+__device__ __forceinline__ bool wait_rows(const StepParams& P, int row, int k,
+                                          volatile int* abort) {
+  const int2 dr = P.row_deps[row];
+  long long t0 = 0;
+  bool first = true;
+#pragma unroll 1
+  while (true) {
+    bool ready = true;
+#pragma unroll 1
+    for (int r = dr.x; r <= dr.y; ++r)
+      if (ld_relaxed_gpu(P.row_done + r) < k * P.row_units[r]) ready = false;
+    if (ready) break;
+    if (first) {
+      t0 = clock64();
+      first = false;
+    }
+    if (*abort || clock64() - t0 > kWaitBudget) return false;
+    __nanosleep(128);
+  }
+  fence_acq_rel_gpu();
+  fence_proxy_async_global();
+  return true;
+}
+
 #ifdef FDW_DEBUG_VERIFY
 // Debug builds only: compare a staged value with the global field it came from.
 __device__ int g_dbg_count;
@@ -172,7 +213,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
                                          const unsigned char* csmem, uint32_t cfull0,
                                          uint32_t cempty0, Cursor& cc,
                                          volatile int* abort_flag, int lane, const Lanes L,
-                                         float& tmax, uint32_t tq) {
+                                         float& tmax, uint32_t tq, const StepCtx sc) {
   static_assert(!TQ || (NY == 1 && !XU), "the tensor-memory queue holds one row per thread");
   constexpr int TZ = kTZ;
   constexpr int R4 = Halo<R>::R4;
@@ -228,7 +269,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
         for (int v = 0; v < kVZ; ++v) qv[j][v][i] = pick(cv, v);
       }
 #ifdef FDW_DEBUG_VERIFY
-      dbg_check("warm", cv.x, d->u, (long long)P.cur * d->uslot, un.x0 - R + i, un.y0 + r0 + j,
+      dbg_check("warm", cv.x, d->u, (long long)sc.cur * d->uslot, un.x0 - R + i, un.y0 + r0 + j,
                 z, d->nx, ny, nz, nzp, u);
 #endif
     }
@@ -239,7 +280,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
   if (!ok) return false;
   cb.skip(R, S);
 
-  float* uo = d->u + (long long)P.out * d->uslot;
+  float* uo = d->u + (long long)sc.out * d->uslot;
   float* acc = d->acc;
   const float* eta_x = d->eta;
   float ex_next = etaf ? 0.f : eta_x[un.x0];  // x part of the damping, one plane ahead
@@ -280,7 +321,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
             for (int v = 0; v < kVZ; ++v) qv[j][v][(t + 2 * R) % Q] = pick(cv, v);
           }
 #ifdef FDW_DEBUG_VERIFY
-          dbg_check("ahead", cv.x, d->u, (long long)P.cur * d->uslot, x + R, un.y0 + r0 + j, z,
+          dbg_check("ahead", cv.x, d->u, (long long)sc.cur * d->uslot, x + R, un.y0 + r0 + j, z,
                     d->nx, ny, nz, nzp, u);
 #endif
         }
@@ -450,6 +491,7 @@ step_kernel(const __grid_constant__ StepParams P) {
   // the producer before the stage's first arrival, read by the consumers
   __shared__ Unit s_unit[kMaxStages];
   __shared__ int s_uidx[kMaxStages];
+  __shared__ int s_step[kMaxStages];  // the step of that unit (kPersist)
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const int S = P.stages;
@@ -505,16 +547,30 @@ step_kernel(const __grid_constant__ StepParams P) {
       int issued = 0, issued_c = 0;
       const uint32_t bytes_u = YW * ZW * 4;
       const bool stall = (P.flags & kTestStall) != 0;
+      // tickets: units of the launch's step, or (kPersist) (step, unit) pairs
+      // in step order, ticket t = k nunits + u for step step0 + k
+      const bool persist = (P.flags & kPersist) != 0;
+      const int total = persist ? (P.step_end - P.step0) * P.nunits : P.nunits;
       auto grab = [&](int after) { return P.ticket ? atomicAdd(P.ticket, 1) : after + (int)gridDim.x; };
-      int u = stall ? P.nunits : (P.ticket ? atomicAdd(P.ticket, 1) : (int)blockIdx.x);
+      int t = stall ? total : (P.ticket ? atomicAdd(P.ticket, 1) : (int)blockIdx.x);
       bool failed = false;
-      while (u < P.nunits && !failed) {
+      while (t < total && !failed) {
+        const int k = persist ? t / P.nunits : 0;
+        const int u = t - k * P.nunits;
+        const StepCtx sc = step_ctx(P, P.step0 + k);
         const Unit un = P.units[u];
         const ShotDesc* d = P.shots + un.shot;
         const uint32_t bytes_in = TY * TZ * 4 + TY * TZ * (d->mtype == kF32 ? 4 : 2) +
                                   (GRAD ? 2 * TY * TZ * 4 : 0) +
                                   ((P.flags & kEtaField) ? TY * TZ * 4 : 0);
-        int next = P.nunits;
+        // the planes this unit reads were written by the previous step
+        if (persist && k > 0 && !wait_rows(P, un.row, k, abort_flag)) {
+          atomicOr(P.err, kErrTimeoutEmpty);
+          *abort_flag = 1;
+          failed = true;
+          break;
+        }
+        int next = total;
         for (int p = un.x0 - R; p < un.x1 + R; ++p) {
           const uint32_t full = full0 + 8 * c.stage, empty = empty0 + 8 * c.stage;
           if (issued >= S && !wait_or_abort(empty, c.phase ^ 1u, abort_flag)) {
@@ -526,18 +582,19 @@ step_kernel(const __grid_constant__ StepParams P) {
           if (p == un.x0 - R) {
             s_unit[c.stage] = un;
             s_uidx[c.stage] = u;
+            s_step[c.stage] = P.step0 + k;
           }
           // the next unit is claimed while the last plane of this one is in
           // flight: late enough to leave it to a CTA that is free earlier,
           // early enough to hide the atomic behind the stages still queued
-          if (p == un.x1 + R - 1) next = grab(u);
+          if (p == un.x1 + R - 1) next = grab(t);
           // the per-plane tiles of plane q: with the halo plane q itself, or
           // (SPLIT) in the second ring together with the halo plane q + R
           const int q = SPLIT ? p - R : p;
           const bool inner = q >= un.x0 && q < un.x1;
           mbar_arrive_expect_tx(full, bytes_u + (!SPLIT && inner ? bytes_in : 0u));
           const uint32_t sb = smem_u32(smem + c.stage * P.stage_bytes);
-          tma_load_4d(sb, &d->tm_uh, un.z0 - R4, un.y0 - R, p, P.cur, full);
+          tma_load_4d(sb, &d->tm_uh, un.z0 - R4, un.y0 - R, p, sc.cur, full);
           ++issued;
           c.next(S);
           if (inner) {
@@ -553,7 +610,7 @@ step_kernel(const __grid_constant__ StepParams P) {
               mbar_arrive_expect_tx(tfull, bytes_in);
               tb = smem_u32(csmem + c2.stage * P.cstage_bytes);
             }
-            tma_load_4d(tb + P.off_p, &d->tm_uc, un.z0, un.y0, q, P.prev, tfull);
+            tma_load_4d(tb + P.off_p, &d->tm_uc, un.z0, un.y0, q, sc.prev, tfull);
             tma_load_3d(tb + P.off_m, &d->tm_m, un.z0, un.y0, q, tfull);
             if (GRAD) {
               tma_load_4d(tb + P.off_f, &d->tm_f, un.z0, un.y0, q, P.fslot, tfull);
@@ -566,7 +623,7 @@ step_kernel(const __grid_constant__ StepParams P) {
             }
           }
         }
-        u = next;
+        t = next;
       }
       // end marker: a stage that carries no data and unit index -1
       if (!failed && !stall) {
@@ -603,20 +660,21 @@ step_kernel(const __grid_constant__ StepParams P) {
       const int u = s_uidx[ca.stage];
       if (u < 0) break;
       const Unit un = s_unit[ca.stage];
+      const StepCtx sc = step_ctx(P, s_step[ca.stage]);
       const ShotDesc* d = P.shots + un.shot;
       const int mtype = d->mtype;
       if (mtype == kF16)
         ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, __half>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
-                                               abort_flag, lane, L, tmax, tq);
+                                               abort_flag, lane, L, tmax, tq, sc);
       else if (mtype == kBF16)
         ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, __nv_bfloat16>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
-                                                      abort_flag, lane, L, tmax, tq);
+                                                      abort_flag, lane, L, tmax, tq, sc);
       else if (!XU && (un.flags & kUnitUndamped))  // every point of the unit undamped
         ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, float, false>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
-                                                     abort_flag, lane, L, tmax, tq);
+                                                     abort_flag, lane, L, tmax, tq, sc);
       else
         ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, float>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
-                                              abort_flag, lane, L, tmax, tq);
+                                              abort_flag, lane, L, tmax, tq, sc);
       if (!ok) break;
 
       // ---- unit tail: injection into u^{n+1} and sampling of u^n ----
@@ -627,10 +685,10 @@ step_kernel(const __grid_constant__ StepParams P) {
       const bool etaf = (P.flags & kEtaField) != 0;
       if (P.flags & kInject) {
         const int ib = P.inj_ptr[u], ie = P.inj_ptr[u + 1];
-        const float* A = d->inj_a + (long long)P.inj_row * d->inj_ld;
-        const float* B = (P.flags & kInjectDiff) ? d->inj_b + (long long)P.inj_row * d->inj_ld
+        const float* A = d->inj_a + (long long)sc.inj_row * d->inj_ld;
+        const float* B = (P.flags & kInjectDiff) ? d->inj_b + (long long)sc.inj_row * d->inj_ld
                                                  : nullptr;
-        float* uo = d->u + (long long)P.out * d->uslot;
+        float* uo = d->u + (long long)sc.out * d->uslot;
         const InjNode* nodes = P.inj_nodes;
         const InjTerm* terms = P.inj_terms;
         const void* mp = d->m;
@@ -694,8 +752,8 @@ step_kernel(const __grid_constant__ StepParams P) {
       }
       if (P.flags & kSample) {
         const int sbg = P.smp_ptr[u], se = P.smp_ptr[u + 1];
-        const float* uc = d->u + (long long)P.cur * d->uslot;
-        float* out = d->smp_out + (long long)P.smp_row * d->smp_ld;
+        const float* uc = d->u + (long long)sc.cur * d->uslot;
+        float* out = d->smp_out + (long long)sc.smp_row * d->smp_ld;
         for (int i = sbg + tid; i < se; i += NCONS) {
           const int j = P.smp_pts[i];
           const int bx = d->pt_base[3 * j], by = d->pt_base[3 * j + 1], bz = d->pt_base[3 * j + 2];
@@ -707,11 +765,25 @@ step_kernel(const __grid_constant__ StepParams P) {
             if (wc != 0.f) {
               const long long off =
                   ((long long)(bx + ((cc >> 2) & 1)) * ny + (by + ((cc >> 1) & 1))) * nzp + bz + (cc & 1);
-              acc = fmaf(wc, uc[off], acc);
+              // at the L2 (kPersist: the field was written by other CTAs
+              // within this launch, after this SM may have cached an older
+              // step's values of the same slot)
+              acc = fmaf(wc, __ldcg(uc + off), acc);
             }
           }
           out[j] = acc;
         }
+      }
+      if (P.flags & kPersist) {
+        // every consumer's writes of this unit (updated planes, injected
+        // nodes, samples) come before the unit counts as finished
+        mbar_arrive(tail);
+        if (!cwait<TQ>(tail, tail_phase, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tail_phase ^= 1u;
+        if (tid == 0) red_release_add_gpu(P.row_done + un.row, 1);
       }
     }
     if (!ok) {

@@ -30,6 +30,10 @@ enum StepFlags : int {
   kTestStall = 16,   // test hook: the producer issues no loads, so every consumer
                      // wait runs out of its clock budget and reports an error
   kAbsMax = 32,      // fold max |u^{n+1}| of every unit into amax[amax_slot] of its shot
+  kPersist = 64,     // forward role only: one launch runs the steps [step0, step_end);
+                     // tickets run over (step, unit), step by step, and a unit of
+                     // step n + 1 starts once the rows of units it reads have
+                     // finished step n (row_done counts finished units per row)
 };
 
 // Per-shot description; lives in device memory, 128-byte aligned (tensor maps).
@@ -66,7 +70,8 @@ struct Unit {
   int x0, x1;
   int y0, z0;
   int flags;           // kUnitUndamped: eta = 0 at every grid point of the unit
-  int pad[2];
+  int row;             // the unit's row: one x chunk of one shot, all its column tiles
+  int pad;
 };
 
 enum UnitFlags : int { kUnitUndamped = 1 };
@@ -119,6 +124,12 @@ struct StepParams {
   float csum;          // sum of the centre weights over the axes
   float w[3][kMaxR + 1];  // dt^2 c_k / h_a^2, k = 0..r (k = 0 unused; see csum)
   int* err;            // error word (0 = fine)
+  // kPersist: steps of the launch, finished units per row (zero before the
+  // launch), the rows [lo, hi] whose planes a row's units read, units per row
+  int step0, step_end;
+  int* row_done;
+  const int2* row_deps;
+  const int* row_units;
 };
 
 // Bits of the device error word: a consumer (full) or producer (empty) wait gave up.

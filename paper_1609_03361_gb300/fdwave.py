@@ -69,6 +69,7 @@ _SIGS = [
     ("fdw_autotune", _I, [_P, _I]),
     ("fdw_set_tiling", _I, [_P, _I, _I, _I]),
     ("fdw_get_tiling", _I, [_P, ctypes.POINTER(_I)]),
+    ("fdw_set_persistent", _I, [_P, _I]),
     ("fdw_set_time_blocking", _I, [_P, _I, _I, _I, _I]),
     ("fdw_get_time_blocking", _I, [_P, ctypes.POINTER(_I)]),
     ("fdw_batch_create", _I, [ctypes.POINTER(_P), _I, _PP]),
@@ -304,6 +305,10 @@ def fdw_autotune(ctx, steps=10):
 
 def fdw_set_tiling(ctx, tile=-1, xchunk=0, stages=0):
     _check(lib().fdw_set_tiling(ctx, int(tile), int(xchunk), int(stages)), ctx)
+
+
+def fdw_set_persistent(ctx, on=True):
+    _check(lib().fdw_set_persistent(ctx, 1 if on else 0), ctx)
 
 
 def fdw_set_time_blocking(ctx, steps_per_pass, variant=-1, xchunk=0, stages=0):
@@ -556,6 +561,10 @@ class Solver:
 
     def tiling(self):
         return fdw_get_tiling(self.ctx)
+
+    def set_persistent(self, on=True):
+        """Plain forward runs as one persistent launch over all time steps."""
+        fdw_set_persistent(self.ctx, on)
 
     def set_time_blocking(self, steps_per_pass, variant=-1, xchunk=0, stages=0):
         """Plain forward runs advance two time steps per launch (steps_per_pass=2)."""

@@ -324,13 +324,17 @@ def full_grid_case():
 
 # the autotuner's choice (as in the bench) and the tilings the bench's tuner
 # has picked on the GB300 (tile 4 with x chunks of 80 and 64, 7 stages)
-@pytest.mark.parametrize("tiling", [None, (4, 80, 7), (4, 64, 7), (7, 80, 7)])
-def test_config_3d_256_so8_full_grid_first_steps(fw, full_grid_case, tiling):
+# (the last case runs every step in one persistent launch)
+@pytest.mark.parametrize("tiling,persist", [(None, False), ((4, 80, 7), False),
+                                            ((4, 64, 7), False), ((7, 80, 7), False),
+                                            ((4, 80, 7), True)])
+def test_config_3d_256_so8_full_grid_first_steps(fw, full_grid_case, tiling, persist):
     w, q32, ref, uref = full_grid_case
     dev = torch.device("cuda", 0)
     s = fw.Solver(w.shape, w.spacing, w.space_order, w.nbl, w.dt, w.nt, w.vmax)
     if tiling is not None:
         s.set_tiling(*tiling)
+    s.set_persistent(persist)
     s.set_model(torch.from_numpy(w.m.astype(np.float32)).to(dev))
     s.set_sources(w.src)
     s.set_receivers(w.rec)

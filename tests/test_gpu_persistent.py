@@ -1,0 +1,125 @@
+"""Plain forward modelling as one persistent launch over all time steps
+(fdw_set_persistent): the same scheme and the same arithmetic per point as
+one launch per step, only scheduled differently, so traces and wavefields
+must be bit for bit those of the per-step loop, and within 1e-4 of the FP64
+oracle."""
+import numpy as np
+import pytest
+
+from problems import Problem, assert_close
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def fw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_03361_gb300 import build, fdwave
+    build.build()
+    fdwave.lib()
+    return fdwave
+
+
+def _fwd(fw, pb, persist, tiling=None):
+    s = pb.solver(fw, tiling=tiling)
+    s.set_persistent(persist)
+    rec = s.forward(pb.q32)
+    u = s.wavefield(0)
+    s.sync()
+    s.close()
+    return rec, u
+
+
+@pytest.mark.parametrize("p", [2, 4, 8, 12, 16])
+def test_persistent_equals_per_step_all_orders(fw, p):
+    pb = Problem((37, 45, 29), 10.0, p, 8, 70, nsrc=2, nrec=9, seed=100 + p)
+    rec1, u1 = _fwd(fw, pb, False)
+    rec2, u2 = _fwd(fw, pb, True)
+    assert np.array_equal(rec1, rec2) and np.array_equal(u1, u2)
+    ref, uref = pb.oracle_forward(final=True)
+    assert_close(rec2, ref, TOL, "traces")
+    assert_close(u2, uref, TOL, "wavefield")
+
+
+@pytest.mark.parametrize("tiling", [(0, 0, 0), (4, 8, 0), (4, 13, 7), (6, 9, 10), (7, 11, 0),
+                                    (8, 0, 0), (1, 0, 0), (5, 7, 9)])
+def test_persistent_equals_per_step_tilings(fw, tiling):
+    """Short x chunks give many rows, so units of a later step run while the
+    previous step is still in progress elsewhere in the grid."""
+    pb = Problem((40, 51, 35), 12.5, 8, 6, 60, nsrc=3, nrec=12, seed=11)
+    rec1, u1 = _fwd(fw, pb, False, tiling)
+    rec2, u2 = _fwd(fw, pb, True, tiling)
+    assert np.array_equal(rec1, rec2) and np.array_equal(u1, u2)
+
+
+def test_persistent_2d_and_short_runs(fw):
+    pb = Problem((61, 57), 10.0, 4, 20, 200, nsrc=1, nrec=11, seed=3)
+    rec1, u1 = _fwd(fw, pb, False)
+    rec2, u2 = _fwd(fw, pb, True)
+    assert np.array_equal(rec1, rec2) and np.array_equal(u1, u2)
+    for nt in (1, 2, 3):
+        pb = Problem((20, 21, 22), 10.0, 8, 3, nt, nsrc=1, nrec=3, seed=nt)
+        rec1, u1 = _fwd(fw, pb, False)
+        rec2, u2 = _fwd(fw, pb, True)
+        assert np.array_equal(rec1, rec2) and np.array_equal(u1, u2)
+
+
+def test_persistent_points_on_chunk_edges(fw):
+    """Sources and receivers on and next to x-chunk boundaries: the injected
+    nodes of one unit and the sampled corners of the next are read across
+    rows that finish at different times."""
+    pb = Problem((44, 30, 33), 10.0, 8, 4, 80, nsrc=1, nrec=4, seed=7)
+    lx = 8
+    xs = [(i * lx - pb.nbl) * pb.h + d for i in (2, 3, 4) for d in (-10.0, -3.0, 0.0, 4.0)]
+    xs = [x for x in xs if 0.0 <= x <= (pb.shape[0] - 1) * pb.h]
+    pts = np.array([[x, 0.4 * (pb.shape[1] - 1) * pb.h, 0.6 * (pb.shape[2] - 1) * pb.h]
+                    for x in xs])
+    pb.rec = np.vstack([pb.rec, pts])
+    pb.src = np.vstack([pb.src, pts[:3]])
+    pb.q32 = np.concatenate([pb.q32, pb.q32[:, :1].repeat(3, axis=1)], axis=1)
+    rec1, u1 = _fwd(fw, pb, False, (4, lx, 0))
+    rec2, u2 = _fwd(fw, pb, True, (4, lx, 0))
+    assert np.array_equal(rec1, rec2) and np.array_equal(u1, u2)
+    ref, uref = pb.oracle_forward(final=True)
+    assert_close(rec2, ref, TOL, "traces")
+    assert_close(u2, uref, TOL, "wavefield")
+
+
+def test_persistent_batch_of_uneven_shots(fw):
+    import oracle
+    shapes = [(21, 24, 19), (30, 17, 26), (18, 18, 33)]
+    pbs = [Problem(sh, 12.5, 8, 5, 60, nsrc=1, nrec=5, seed=50 + i) for i, sh in enumerate(shapes)]
+    dt = min(pb.dt for pb in pbs)
+    vmax = max(pb.vmax for pb in pbs)
+    for pb in pbs:
+        pb.dt = dt
+        pb.vmax = vmax
+        pb.setup = oracle.Setup(pb.shape, pb.h, pb.p, pb.nbl, dt, pb.nt)
+    outs = []
+    for persist in (False, True):
+        solvers = [pb.solver(fw) for pb in pbs]
+        for s in solvers:
+            s.set_persistent(persist)
+        b = fw.Batch(solvers)
+        outs.append(b.forward([pb.q32 for pb in pbs]))
+        for s in solvers:
+            s.sync()
+        b.close()
+        for s in solvers:
+            s.close()
+    for a, c, pb in zip(outs[0], outs[1], pbs):
+        assert np.array_equal(a, c)
+        assert_close(c, pb.oracle_forward(), TOL, "traces")
+
+
+def test_persistent_rejected_on_slabs(fw):
+    pb = Problem((24, 20, 22), 10.0, 4, 4, 20, nsrc=1, nrec=3, seed=3)
+    s = fw.Solver(pb.shape, pb.h, 4, 4, pb.dt, pb.nt, pb.vmax, slab=(0, 15))
+    with pytest.raises(fw.FdwError) as e:
+        s.set_persistent(True)
+    assert e.value.status == 9
+    s.close()
