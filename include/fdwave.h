@@ -219,11 +219,16 @@ fdw_status fdw_set_checkpoint_budget(fdw_ctx* ctx, int max_pairs);
  * nslots < 0, cap < 0 or actions NULL with cap > 0.  Host only. */
 int fdw_checkpoint_schedule(int nseg, int nslots, int* actions, int cap);
 
-/* Force a tile configuration: tile index (0..8, -1 = default; 3 is meant for
+/* Force a tile configuration: tile index (0..9, -1 = default; 3 is meant for
  * 2D grids, 6 keeps per-plane tiles in a second ring, 7 and 8 are 4 and 6
- * with the x-direction queue in tensor memory), x-chunk length (0 = default) and pipeline depth of the forward
- * and adjoint steps (>= r + 2 with r = space_order / 2, 0 = default; the
- * gradient step picks its own).  FDW_ERR_ARG outside these ranges. */
+ * with the x-direction queue in tensor memory, 9 is 7 with each pipeline
+ * stage holding exactly one plane's reads: the halo plane x, its tiles and
+ * the centre tile of plane x + r), x-chunk length (0 = default) and pipeline
+ * depth of the forward and adjoint steps (>= r + 2 with r = space_order / 2,
+ * >= 2 for tile 9, 0 = default; the gradient step picks its own and runs
+ * tile 9 as tile 7).  Every tile computes each point with the same arithmetic,
+ * so the results do not depend on the tiling, bit for bit.  FDW_ERR_ARG
+ * outside these ranges. */
 fdw_status fdw_set_tiling(fdw_ctx* ctx, int tile, int xchunk, int stages);
 
 /* Run plain forward modelling (fdw_forward, and fdw_batch_forward when every

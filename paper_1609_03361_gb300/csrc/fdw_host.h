@@ -253,6 +253,7 @@ inline int bucket_points(const int* unit_of, int n, int U, int* ptr, int* pts) {
 // the x stencil ahead of the plane being updated).
 struct StageLayout {
   int off_p, off_m, off_f, off_a, off_e;  // tile offsets inside their stage
+  int off_c;    // centre tile of plane x + r (tiles with `ca`; 0 otherwise)
   int bytes;    // halo-ring stage
   int cbytes;   // second-ring stage (0: no second ring)
   int r;
@@ -285,9 +286,21 @@ inline StageLayout stage_layout(int r, int tile, int mt_bytes, bool grad, bool e
   if (grad) off += round128(TY * kTZ * 4);
   L.off_e = off;
   if (etaf) off += round128(TY * kTZ * 4);
+  L.off_c = 0;
+  if (!split && kTiles[tile].ca) {
+    L.off_c = off;
+    off += round128(TY * kTZ * 4);
+  }
   L.bytes = split ? halo : off;
   L.cbytes = split ? off : 0;
   return L;
+}
+
+// Fewest pipeline stages of a tile: the halo plane of plane x stays staged
+// until x is updated while planes up to x + r are read ahead, unless the
+// centre values come in tiles of their own (then any two stages pipeline).
+inline int min_stages(int r, int tile, bool grad) {
+  return (!grad && kTiles[tile].ca) ? 2 : r + 2;
 }
 
 // Dynamic shared memory of a launch: the stages of both rings, their full

@@ -16,23 +16,34 @@ namespace fdw {
 // Tile 6 is tile 4 with the per-plane tiles in a second ring: less shared
 // memory per CTA, which lets the high orders (r >= 6) hold three CTAs per SM.
 // Tiles 7 and 8 are tiles 4 and 6 with the x queue in tensor memory instead
-// of registers (no per-plane queue moves; the CTA allocates tq_cols columns).
+// of registers (no per-plane queue moves; the CTA allocates tq_columns).
+// Tile 9 is tile 7 with stages that hold exactly what one plane's update
+// reads: the halo plane x, the tiles of plane x and the centre tile of plane
+// x + r (the values that join the x queue), so every stage is freed after one
+// plane instead of staying r + 1 planes, and a few stages pipeline; it also
+// forms the neighbour pair sums two at a time (fewer registers), so at the
+// high orders more CTAs fit on an SM (the gradient step runs as tile 7).
 struct TileShape {
   int ny_pts;
   int warps;
   bool split;  // the forward and adjoint steps also keep the per-plane tiles
                // in a second ring (gradient steps always do)
   bool tq;     // x queue in tensor memory
+  bool ca;     // centre tile of plane x + r staged with plane x (forward, adjoint)
 };
-constexpr int kNumTiles = 9;
-constexpr TileShape kTiles[kNumTiles] = {{1, 4, false, false}, {2, 4, false, false},
-                                         {1, 8, false, false}, {1, 1, false, false},
-                                         {1, 4, false, false}, {2, 2, false, false},
-                                         {1, 4, true, false},  {1, 4, false, true},
-                                         {1, 4, true, true}};
-// Tensor-memory columns a CTA of a tq tile allocates at radius r (the ring of
-// 2 (2r+1) planes of four values, rounded up to a power of two); an SM has 512.
-__host__ __device__ constexpr int tq_columns(int r) { return 8 * (2 * r + 1) <= 128 ? 128 : 256; }
+constexpr int kNumTiles = 10;
+constexpr TileShape kTiles[kNumTiles] = {
+    {1, 4, false, false, false}, {2, 4, false, false, false}, {1, 8, false, false, false},
+    {1, 1, false, false, false}, {1, 4, false, false, false}, {2, 2, false, false, false},
+    {1, 4, true, false, false},  {1, 4, false, true, false},  {1, 4, true, true, false},
+    {1, 4, false, true, true}};
+// Tensor-memory columns a CTA of a tq tile allocates at radius r: the ring of
+// 2r+1 planes of four values plus the second copies that a window of 2r
+// planes starting at any slot reads past the ring's end (slots 0 .. 2r-2),
+// 16 r columns, rounded up to a power of two of at least 32; an SM has 512.
+__host__ __device__ constexpr int tq_columns(int r) {
+  return 16 * r <= 32 ? 32 : (16 * r <= 64 ? 64 : 128);
+}
 constexpr int tile_rows(const TileShape& t) { return 4 * t.ny_pts * t.warps; }
 
 // Kernel registry: one translation unit per stencil radius.

@@ -247,7 +247,7 @@ struct Plan {
     const void* fn;
     int grid, threads, stages, cstages, cstage_bytes;
     size_t smem;
-    int stage_bytes, off_p, off_m, off_f, off_a, off_e;
+    int stage_bytes, off_p, off_m, off_f, off_a, off_e, off_c;
     int resident;  // CTAs that fit on the device at once
   };
   std::map<std::tuple<int, int, int, int, int, int>, LaunchInfo> launch_cache;
@@ -529,7 +529,7 @@ static int max_stages(const Plan& pl, int tile) {
   const StageLayout L = stage_layout(pl.r, tile, 4, false, true);
   const int cap = device_smem_optin(pl.device) - 1024;  // static shared memory and slack
   int s = 2 * pl.r + 8;
-  while (s > pl.r + 2 && (int)smem_bytes(L, s) > cap) --s;
+  while (s > min_stages(pl.r, tile, false) && (int)smem_bytes(L, s) > cap) --s;
   return s;
 }
 
@@ -542,7 +542,8 @@ static void choose_default_tiling(Plan& pl) {
   pl.tile = pl.tile_req >= 0 ? pl.tile_req : (all2d ? 3 : 4);
   const int ms = max_stages(pl, pl.tile);
   pl.stages = pl.stages_req > 0 ? std::min(pl.stages_req, ms) : std::min(pl.r + 4, ms);
-  if (pl.stages < pl.r + 2) fail(FDW_ERR_ARG, "pipeline too shallow for this order");
+  if (pl.stages < min_stages(pl.r, pl.tile, false))
+    fail(FDW_ERR_ARG, "pipeline too shallow for this order");
   if (pl.lx_req > 0) {
     pl.lx = pl.lx_req;
     return;
@@ -941,6 +942,7 @@ static const Plan::LaunchInfo& launch_info(Plan& pl, bool grad) {
   li.off_f = L.off_f;
   li.off_a = L.off_a;
   li.off_e = L.off_e;
+  li.off_c = L.off_c;
   return pl.launch_cache.emplace(key, li).first->second;
 }
 
@@ -1023,6 +1025,7 @@ static void launch_step(Plan& pl, const StepArgs& a, cudaStream_t s) {
   P.off_f = li.off_f;
   P.off_a = li.off_a;
   P.off_e = li.off_e;
+  P.off_c = li.off_c;
   stencil_weights(pl, P.w, &P.csum, &P.dt2);
   P.err = pl.d_err;
   const bool persist = (a.flags & kPersist) != 0;
@@ -1922,7 +1925,7 @@ static void plan_autotune(Plan& pl, int steps) {
       nxmax = std::max(nxmax, c->nx);
     }
     std::vector<int> tiles =
-        all2d ? std::vector<int>{3} : std::vector<int>{0, 1, 2, 4, 5, 6, 7, 8};
+        all2d ? std::vector<int>{3} : std::vector<int>{0, 1, 2, 4, 5, 6, 7, 8, 9};
     std::vector<int> lxs = {16, 32, 48, 64, 80, 96, 128, nxmax};
     cudaStream_t s = pl.cap;
     cudaEvent_t e0, e1;
@@ -1999,8 +2002,15 @@ static void plan_autotune(Plan& pl, int steps) {
     std::vector<std::tuple<float, int, int, int>> cand;
     for (int t : tiles) {
       const int ms = max_stages(pl, t);
-      for (int extra : {1, 2, 3}) {
-        const int st = std::min(pl.r + 1 + extra, ms);
+      // r + 2 .. r + 4 stages; a tile whose stages hold one plane's reads
+      // (ca) pipelines from two: 3, 5 and 7 stages (4, 5, 6 above radius 4,
+      // where three of its CTAs fit on an SM with up to six)
+      std::vector<int> sts;
+      for (int extra : {1, 2, 3})
+        sts.push_back(std::min(kTiles[t].ca ? (pl.r > 4 ? 3 + extra : 1 + 2 * extra)
+                                            : pl.r + 1 + extra, ms));
+      sts.erase(std::unique(sts.begin(), sts.end()), sts.end());
+      for (int st : sts) {
         for (int lx : lxs) {
           if (lx > nxmax && lx != nxmax) continue;
           cand.emplace_back(time_config(t, lx, st, steps), t, lx, st);
@@ -2464,7 +2474,8 @@ fdw_status fdw_set_tiling(fdw_ctx* c, int tile, int xchunk, int stages) {
   return guard(&c->err, [&] {
     if (tile < -1 || tile >= kNumTiles) fail(FDW_ERR_ARG, "tile index out of range");
     if (xchunk < 0 || stages < 0) fail(FDW_ERR_ARG, "negative tiling value");
-    if (stages > 0 && stages < c->r + 2) fail(FDW_ERR_ARG, "stages must be >= r + 2");
+    if (stages > 0 && stages < min_stages(c->r, tile < 0 ? 0 : tile, false))
+      fail(FDW_ERR_ARG, "stages must be >= r + 2 (>= 2 for tile 9)");
     c->tile = tile;
     c->xchunk = xchunk;
     c->stages = stages;

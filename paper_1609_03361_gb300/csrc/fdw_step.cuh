@@ -29,8 +29,9 @@
 //    during this step) and record the sampled points of u^n.
 // With TQ the x queue lives in tensor memory instead of registers: each
 // thread owns one TMEM lane, where a ring of 2r+1 planes (four values each) is
-// stored twice over, so that the 2r planes x-r .. x+r-1 around the plane being
-// updated are always 8r consecutive columns, read with one load per plane.
+// stored with a second copy of slots 0 .. 2r-2 after its end, so that the 2r
+// planes x-r .. x+r-1 around the plane being updated are always 8r
+// consecutive columns (16 r columns in all), read with one load per plane.
 // A plane is written once (two 16-byte stores) when it arrives, and nothing
 // shifts: the register queue costs 2r moves per point and plane, and 2r+1
 // live registers per point.
@@ -204,8 +205,12 @@ __device__ __forceinline__ void dbg_check(const char* what, float got, const flo
 // one update per plane of [x0, x1).  XU: the x loop is unrolled by the queue
 // length 2R+1 so that the queue slots rotate; otherwise the queue shifts by one
 // slot per plane (smaller code).  SPLIT: the per-plane tiles come from the
-// second ring (cursor cc).  Returns false if a wait gave up.
-template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT, bool TQ, typename MT,
+// second ring (cursor cc).  CA: the stage of plane x also carries the centre
+// tile of plane x + R, so the unit takes 2R warm-up stages (centre tiles of
+// planes x0-R .. x0+R-1) and then exactly one stage per updated plane, each
+// released as soon as that plane is done (cursor ca alone).  Returns false if
+// a wait gave up.
+template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT, bool TQ, bool CA, typename MT,
           bool DAMP = true>
 __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, const ShotDesc* d,
                                          int u, const unsigned char* smem, uint32_t full0,
@@ -215,6 +220,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
                                          volatile int* abort_flag, int lane, const Lanes L,
                                          float& tmax, uint32_t tq, const StepCtx sc) {
   static_assert(!TQ || (NY == 1 && !XU), "the tensor-memory queue holds one row per thread");
+  static_assert(!CA || (TQ && !SPLIT && !GRAD), "centre tiles are staged for the tensor-memory queue");
   constexpr int TZ = kTZ;
   constexpr int R4 = Halo<R>::R4;
   constexpr int ZW = Halo<R>::ZW;
@@ -250,20 +256,22 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
   // x queue of centre values: slot (p - x0 + R) mod Q holds plane p (XU), or
   // slot i holds plane x - R + i (shift)
   // (with TQ: the ring slot of plane p is (p - x0 + R) mod Q, columns
-  // 4 slot and 4 (slot + Q) of the thread's lane from tq)
+  // 4 slot and, for slots 0 .. 2R-2, 4 (slot + Q) of the thread's lane from tq)
   float qv[NY][kVZ][TQ ? 1 : Q];
   if constexpr (TQ) tmem_wait_st();  // the previous unit's last stores are done
   bool ok = true;
 #pragma unroll
   for (int i = 0; i < 2 * R; ++i) {
     if (ok) ok = cwait<TQ>(full0 + 8 * ca.stage, ca.phase, abort_flag);
-    const float* U = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes);
+    const float* U = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes +
+                                                    (CA ? P.off_c : 0));
 #pragma unroll
     for (int j = 0; j < NY; ++j) {
-      const float4 cv = ok ? lds4(U + (r0 + j + R) * ZW + R4 + zl) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int ci = CA ? (r0 + j) * TZ + zl : (r0 + j + R) * ZW + R4 + zl;
+      const float4 cv = ok ? lds4(U + ci) : make_float4(0.f, 0.f, 0.f, 0.f);
       if constexpr (TQ) {
         tmem_st4(tq + 4 * i, cv);
-        tmem_st4(tq + 4 * (i + Q), cv);
+        if (i <= 2 * R - 2) tmem_st4(tq + 4 * (i + Q), cv);  // read past the ring's end
       } else {
 #pragma unroll
         for (int v = 0; v < kVZ; ++v) qv[j][v][i] = pick(cv, v);
@@ -274,11 +282,11 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
 #endif
     }
     const int p = un.x0 - R + i;
-    if (p < un.x0 || p >= un.x1) release_stage(empty0 + 8 * ca.stage, lane);
+    if (CA || p < un.x0 || p >= un.x1) release_stage(empty0 + 8 * ca.stage, lane);
     ca.next(S);
   }
   if (!ok) return false;
-  cb.skip(R, S);
+  if constexpr (!CA) cb.skip(R, S);
 
   float* uo = d->u + (long long)sc.out * d->uslot;
   float* acc = d->acc;
@@ -310,10 +318,11 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
       float4 ahead[NY];
       (void)ahead;
       {
-        const float* Ua = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes);
+        const float* Ua = reinterpret_cast<const float*>(smem + ca.stage * P.stage_bytes +
+                                                         (CA ? P.off_c : 0));
 #pragma unroll
         for (int j = 0; j < NY; ++j) {
-          const float4 cv = lds4(Ua + (r0 + j + R) * ZW + R4 + zl);
+          const float4 cv = lds4(Ua + (CA ? (r0 + j) * TZ + zl : (r0 + j + R) * ZW + R4 + zl));
           if constexpr (TQ) {
             ahead[j] = cv;
           } else {
@@ -330,7 +339,9 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
         // plane x+R takes the slot of plane x-R-1, outside the window in flight
         const int sa = tq_sl == 0 ? Q - 1 : tq_sl - 1;
         tmem_st4(tq + 4 * sa, ahead[0]);
-        tmem_st4(tq + 4 * (sa + Q), ahead[0]);
+        // the second copy for slots 0 .. 2R-2; the other slots write their
+        // one copy again (no branch around the warp-wide store)
+        tmem_st4(tq + 4 * (sa <= 2 * R - 2 ? sa + Q : sa), ahead[0]);
         tq_sl = tq_sl + 1 == Q ? 0 : tq_sl + 1;
       }
       // a look-ahead plane past the chunk is only needed for its centre
@@ -338,8 +349,9 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
       const int ahead_stage = ca.stage;
       ca.next(S);
 
-      // neighbours in y and z of plane x from the staged halo plane
-      const unsigned char* sb = smem + cb.stage * P.stage_bytes;
+      // neighbours in y and z of plane x from the staged halo plane (CA: the
+      // stage just read, which holds plane x itself)
+      const unsigned char* sb = smem + (CA ? ahead_stage : cb.stage) * P.stage_bytes;
       const float* U = reinterpret_cast<const float*>(sb);
       const unsigned char* tb = sb;  // the plane's own tiles
       if (SPLIT) {
@@ -373,7 +385,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
 #pragma unroll
         for (int j = 0; j < NY; ++j) yr[R + j] = lds4(U + (r0 + j + R) * ZW + R4 + zl);
       }
-      if constexpr (TQ) win.wait();
+      if constexpr (TQ && !CA) win.wait();
 #pragma unroll
       for (int j = 0; j < NY; ++j) {
         float wz[NW];
@@ -391,21 +403,9 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
         float4 ev;
         if (etaf) ev = lds4(reinterpret_cast<const float*>(tb + P.off_e) + li);
         else ev = make_float4(ex + eyz[j][0], ex + eyz[j][1], ex + eyz[j][2], ex + eyz[j][3]);
-#pragma unroll
-        for (int v = 0; v < kVZ; ++v) {
+        // the update of point v from its three axis sums
+        auto finish = [&](int v, float lx, float ly, float lz) {
           const float c = wz[R4 + v];
-          float lx = 0.f, ly = 0.f, lz = 0.f;
-#pragma unroll
-          for (int k = 1; k <= R; ++k) {
-            if constexpr (TQ) {
-              const float xb = k < R ? win.v(4 * (R + k) + v) : pick(ahead[j], v);
-              lx = fmaf(P.w[0][k], win.v(4 * (R - k) + v) + xb, lx);
-            } else {
-              lx = fmaf(P.w[0][k], qv[j][v][(t + R - k) % Q] + qv[j][v][(t + R + k) % Q], lx);
-            }
-            ly = fmaf(P.w[1][k], pick(yr[R + j - k], v) + pick(yr[R + j + k], v), ly);
-            lz = fmaf(P.w[2][k], wz[R4 + v - k] + wz[R4 + v + k], lz);
-          }
           const float lap = fmaf(P.csum, c, lx + ly + lz);
           const float sm = pick(sv, v), prev = pick(pv, v);
           if constexpr (DAMP) {
@@ -417,6 +417,74 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
             val[j][v] = fmaf(sm, lap, 2.f * c) - prev;
           }
           if (GRAD) d2t[j][v] = val[j][v] - 2.f * c + prev;  // second time difference of lambda
+        };
+        if constexpr (CA) {
+          // the neighbour pair sums of two points at a time (fadd2: two
+          // correctly rounded adds, the scalar results), then one FMA per
+          // point and k in the scalar order; the y and z sums first, while
+          // the tensor-memory window is still in flight
+          float ly[kVZ] = {0.f, 0.f, 0.f, 0.f}, lz[kVZ] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int k = 1; k <= R; ++k) {
+            const float4 ym = yr[R + j - k], yp = yr[R + j + k];
+            const float2 ya = __fadd2_rn(make_float2(ym.x, ym.y), make_float2(yp.x, yp.y));
+            const float2 yb = __fadd2_rn(make_float2(ym.z, ym.w), make_float2(yp.z, yp.w));
+            ly[0] = fmaf(P.w[1][k], ya.x, ly[0]);
+            ly[1] = fmaf(P.w[1][k], ya.y, ly[1]);
+            ly[2] = fmaf(P.w[1][k], yb.x, ly[2]);
+            ly[3] = fmaf(P.w[1][k], yb.y, ly[3]);
+            if ((k & 1) == 0) {
+              // R4 -+ k even: the pairs (e, e+1) of both sides are aligned
+              const int m = R4 - k, q = R4 + k;
+              const float2 za = __fadd2_rn(make_float2(wz[m], wz[m + 1]), make_float2(wz[q], wz[q + 1]));
+              const float2 zb = __fadd2_rn(make_float2(wz[m + 2], wz[m + 3]),
+                                           make_float2(wz[q + 2], wz[q + 3]));
+              lz[0] = fmaf(P.w[2][k], za.x, lz[0]);
+              lz[1] = fmaf(P.w[2][k], za.y, lz[1]);
+              lz[2] = fmaf(P.w[2][k], zb.x, lz[2]);
+              lz[3] = fmaf(P.w[2][k], zb.y, lz[3]);
+            } else {
+#pragma unroll
+              for (int v = 0; v < kVZ; ++v)
+                lz[v] = fmaf(P.w[2][k], wz[R4 + v - k] + wz[R4 + v + k], lz[v]);
+            }
+          }
+          win.wait();
+          float lx[kVZ] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int k = 1; k <= R; ++k) {
+            const int i0 = 4 * (R - k), i1 = 4 * (R + k);
+            const float2 ma = make_float2(win.v(i0), win.v(i0 + 1));
+            const float2 mb = make_float2(win.v(i0 + 2), win.v(i0 + 3));
+            const float2 pa = k < R ? make_float2(win.v(i1), win.v(i1 + 1))
+                                    : make_float2(ahead[j].x, ahead[j].y);
+            const float2 pb = k < R ? make_float2(win.v(i1 + 2), win.v(i1 + 3))
+                                    : make_float2(ahead[j].z, ahead[j].w);
+            const float2 xa = __fadd2_rn(ma, pa), xb = __fadd2_rn(mb, pb);
+            lx[0] = fmaf(P.w[0][k], xa.x, lx[0]);
+            lx[1] = fmaf(P.w[0][k], xa.y, lx[1]);
+            lx[2] = fmaf(P.w[0][k], xb.x, lx[2]);
+            lx[3] = fmaf(P.w[0][k], xb.y, lx[3]);
+          }
+#pragma unroll
+          for (int v = 0; v < kVZ; ++v) finish(v, lx[v], ly[v], lz[v]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < kVZ; ++v) {
+            float lx = 0.f, ly = 0.f, lz = 0.f;
+#pragma unroll
+            for (int k = 1; k <= R; ++k) {
+              if constexpr (TQ) {
+                const float xb = k < R ? win.v(4 * (R + k) + v) : pick(ahead[j], v);
+                lx = fmaf(P.w[0][k], win.v(4 * (R - k) + v) + xb, lx);
+              } else {
+                lx = fmaf(P.w[0][k], qv[j][v][(t + R - k) % Q] + qv[j][v][(t + R + k) % Q], lx);
+              }
+              ly = fmaf(P.w[1][k], pick(yr[R + j - k], v) + pick(yr[R + j + k], v), ly);
+              lz = fmaf(P.w[2][k], wz[R4 + v - k] + wz[R4 + v + k], lz);
+            }
+            finish(v, lx, ly, lz);
+          }
         }
         if (GRAD) {
           fw[j] = lds4(reinterpret_cast<const float*>(tb + P.off_f) + li);
@@ -425,14 +493,18 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
       }
       // every read of the staged planes is done: hand them back before the
       // global stores, which only read registers
-      if (SPLIT) {
-        release_stages(empty0 + 8 * cb.stage, cempty0 + 8 * cc.stage, lane);
-        cc.next(P.cstages);
+      if constexpr (CA) {
+        release_stage(empty0 + 8 * ahead_stage, lane);
       } else {
-        release_stage(empty0 + 8 * cb.stage, lane);
+        if (SPLIT) {
+          release_stages(empty0 + 8 * cb.stage, cempty0 + 8 * cc.stage, lane);
+          cc.next(P.cstages);
+        } else {
+          release_stage(empty0 + 8 * cb.stage, lane);
+        }
+        if (x + R >= un.x1) release_stage(empty0 + 8 * ahead_stage, lane);
+        cb.next(S);
       }
-      if (x + R >= un.x1) release_stage(empty0 + 8 * ahead_stage, lane);
-      cb.next(S);
       if (amx) {  // points past the grid compute to zero and do not move the maximum
 #pragma unroll
         for (int j = 0; j < NY; ++j)
@@ -465,7 +537,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
       }
     }
   }
-  cb.skip(R, S);
+  if constexpr (!CA) cb.skip(R, S);
   return true;
 }
 
@@ -473,10 +545,12 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
 // resident CTAs per SM (136 registers a thread), which its smaller shared
 // memory allows; every other instance leaves the register count to the
 // compiler (a minimum of 0 blocks states no constraint).
-template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT = GRAD, bool TQ = false>
+template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT = GRAD, bool TQ = false,
+          bool CA = false>
 __global__ void __launch_bounds__((BY + 1) * 32, (SPLIT && !GRAD && R >= 7 && !TQ) ? 3 : 0)
 step_kernel(const __grid_constant__ StepParams P) {
   static_assert(!TQ || BY == 4, "the tensor-memory queue maps the four consumer warps to the four lane quarters");
+  static_assert(!CA || (TQ && !SPLIT && !GRAD), "centre tiles are staged for the tensor-memory queue");
   constexpr int TZ = kTZ;
   constexpr int TY = 4 * BY * NY;
   constexpr int R4 = Halo<R>::R4;
@@ -571,55 +645,92 @@ step_kernel(const __grid_constant__ StepParams P) {
           break;
         }
         int next = total;
-        for (int p = un.x0 - R; p < un.x1 + R; ++p) {
-          const uint32_t full = full0 + 8 * c.stage, empty = empty0 + 8 * c.stage;
-          if (issued >= S && !wait_or_abort(empty, c.phase ^ 1u, abort_flag)) {
-            atomicOr(P.err, kErrTimeoutEmpty);
-            *abort_flag = 1;
-            failed = true;
-            break;
+        if constexpr (CA) {
+          // 2R warm-up stages with the centre tiles of planes x0-R .. x0+R-1,
+          // then per plane x of the chunk: the centre tile of plane x + R, the
+          // halo plane x and the tiles of x
+          const uint32_t bytes_c = TY * TZ * 4;
+          const int nst = 2 * R + (un.x1 - un.x0);
+          for (int i = 0; i < nst; ++i) {
+            const uint32_t full = full0 + 8 * c.stage, empty = empty0 + 8 * c.stage;
+            if (issued >= S && !wait_or_abort(empty, c.phase ^ 1u, abort_flag)) {
+              atomicOr(P.err, kErrTimeoutEmpty);
+              *abort_flag = 1;
+              failed = true;
+              break;
+            }
+            if (i == 0) {
+              s_unit[c.stage] = un;
+              s_uidx[c.stage] = u;
+              s_step[c.stage] = P.step0 + k;
+            }
+            if (i == nst - 1) next = grab(t);
+            const bool warm = i < 2 * R;
+            const int x = un.x0 + i - 2 * R;               // plane updated (after warm-up)
+            const int pc = warm ? un.x0 - R + i : x + R;   // plane of the centre tile
+            mbar_arrive_expect_tx(full, bytes_c + (warm ? 0u : bytes_u + bytes_in));
+            const uint32_t sb = smem_u32(smem + c.stage * P.stage_bytes);
+            tma_load_4d(sb + P.off_c, &d->tm_uc, un.z0, un.y0, pc, sc.cur, full);
+            if (!warm) {
+              tma_load_4d(sb, &d->tm_uh, un.z0 - R4, un.y0 - R, x, sc.cur, full);
+              tma_load_4d(sb + P.off_p, &d->tm_uc, un.z0, un.y0, x, sc.prev, full);
+              tma_load_3d(sb + P.off_m, &d->tm_m, un.z0, un.y0, x, full);
+              if (P.flags & kEtaField) tma_load_3d(sb + P.off_e, &d->tm_e, un.z0, un.y0, x, full);
+            }
+            ++issued;
+            c.next(S);
           }
-          if (p == un.x0 - R) {
-            s_unit[c.stage] = un;
-            s_uidx[c.stage] = u;
-            s_step[c.stage] = P.step0 + k;
-          }
-          // the next unit is claimed while the last plane of this one is in
-          // flight: late enough to leave it to a CTA that is free earlier,
-          // early enough to hide the atomic behind the stages still queued
-          if (p == un.x1 + R - 1) next = grab(t);
-          // the per-plane tiles of plane q: with the halo plane q itself, or
-          // (SPLIT) in the second ring together with the halo plane q + R
-          const int q = SPLIT ? p - R : p;
-          const bool inner = q >= un.x0 && q < un.x1;
-          mbar_arrive_expect_tx(full, bytes_u + (!SPLIT && inner ? bytes_in : 0u));
-          const uint32_t sb = smem_u32(smem + c.stage * P.stage_bytes);
-          tma_load_4d(sb, &d->tm_uh, un.z0 - R4, un.y0 - R, p, sc.cur, full);
-          ++issued;
-          c.next(S);
-          if (inner) {
-            uint32_t tb = sb, tfull = full;
-            if (SPLIT) {
-              tfull = cfull0 + 8 * c2.stage;
-              if (issued_c >= SC && !wait_or_abort(cempty0 + 8 * c2.stage, c2.phase ^ 1u, abort_flag)) {
-                atomicOr(P.err, kErrTimeoutEmpty);
-                *abort_flag = 1;
-                failed = true;
-                break;
+        } else {
+          for (int p = un.x0 - R; p < un.x1 + R; ++p) {
+            const uint32_t full = full0 + 8 * c.stage, empty = empty0 + 8 * c.stage;
+            if (issued >= S && !wait_or_abort(empty, c.phase ^ 1u, abort_flag)) {
+              atomicOr(P.err, kErrTimeoutEmpty);
+              *abort_flag = 1;
+              failed = true;
+              break;
+            }
+            if (p == un.x0 - R) {
+              s_unit[c.stage] = un;
+              s_uidx[c.stage] = u;
+              s_step[c.stage] = P.step0 + k;
+            }
+            // the next unit is claimed while the last plane of this one is in
+            // flight: late enough to leave it to a CTA that is free earlier,
+            // early enough to hide the atomic behind the stages still queued
+            if (p == un.x1 + R - 1) next = grab(t);
+            // the per-plane tiles of plane q: with the halo plane q itself, or
+            // (SPLIT) in the second ring together with the halo plane q + R
+            const int q = SPLIT ? p - R : p;
+            const bool inner = q >= un.x0 && q < un.x1;
+            mbar_arrive_expect_tx(full, bytes_u + (!SPLIT && inner ? bytes_in : 0u));
+            const uint32_t sb = smem_u32(smem + c.stage * P.stage_bytes);
+            tma_load_4d(sb, &d->tm_uh, un.z0 - R4, un.y0 - R, p, sc.cur, full);
+            ++issued;
+            c.next(S);
+            if (inner) {
+              uint32_t tb = sb, tfull = full;
+              if (SPLIT) {
+                tfull = cfull0 + 8 * c2.stage;
+                if (issued_c >= SC && !wait_or_abort(cempty0 + 8 * c2.stage, c2.phase ^ 1u, abort_flag)) {
+                  atomicOr(P.err, kErrTimeoutEmpty);
+                  *abort_flag = 1;
+                  failed = true;
+                  break;
+                }
+                mbar_arrive_expect_tx(tfull, bytes_in);
+                tb = smem_u32(csmem + c2.stage * P.cstage_bytes);
               }
-              mbar_arrive_expect_tx(tfull, bytes_in);
-              tb = smem_u32(csmem + c2.stage * P.cstage_bytes);
-            }
-            tma_load_4d(tb + P.off_p, &d->tm_uc, un.z0, un.y0, q, sc.prev, tfull);
-            tma_load_3d(tb + P.off_m, &d->tm_m, un.z0, un.y0, q, tfull);
-            if (GRAD) {
-              tma_load_4d(tb + P.off_f, &d->tm_f, un.z0, un.y0, q, P.fslot, tfull);
-              tma_load_3d(tb + P.off_a, &d->tm_a, un.z0, un.y0, q, tfull);
-            }
-            if (P.flags & kEtaField) tma_load_3d(tb + P.off_e, &d->tm_e, un.z0, un.y0, q, tfull);
-            if (SPLIT) {
-              ++issued_c;
-              c2.next(SC);
+              tma_load_4d(tb + P.off_p, &d->tm_uc, un.z0, un.y0, q, sc.prev, tfull);
+              tma_load_3d(tb + P.off_m, &d->tm_m, un.z0, un.y0, q, tfull);
+              if (GRAD) {
+                tma_load_4d(tb + P.off_f, &d->tm_f, un.z0, un.y0, q, P.fslot, tfull);
+                tma_load_3d(tb + P.off_a, &d->tm_a, un.z0, un.y0, q, tfull);
+              }
+              if (P.flags & kEtaField) tma_load_3d(tb + P.off_e, &d->tm_e, un.z0, un.y0, q, tfull);
+              if (SPLIT) {
+                ++issued_c;
+                c2.next(SC);
+              }
             }
           }
         }
@@ -664,16 +775,16 @@ step_kernel(const __grid_constant__ StepParams P) {
       const ShotDesc* d = P.shots + un.shot;
       const int mtype = d->mtype;
       if (mtype == kF16)
-        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, __half>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
+        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, CA, __half>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
                                                abort_flag, lane, L, tmax, tq, sc);
       else if (mtype == kBF16)
-        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, __nv_bfloat16>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
+        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, CA, __nv_bfloat16>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
                                                       abort_flag, lane, L, tmax, tq, sc);
       else if (!XU && (un.flags & kUnitUndamped))  // every point of the unit undamped
-        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, float, false>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
+        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, CA, float, false>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
                                                      abort_flag, lane, L, tmax, tq, sc);
       else
-        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, float>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
+        ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, CA, float>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
                                               abort_flag, lane, L, tmax, tq, sc);
       if (!ok) break;
 

@@ -119,6 +119,8 @@ struct StepParams {
   int cstage_bytes;
   int off_p, off_m, off_f, off_e;  // byte offsets of the per-plane tiles
   int off_a;           // byte offset of the gradient-accumulator tile (gradient)
+  int off_c;           // byte offset of the centre tile of u^n, R planes ahead
+                       // of the stage's own plane (tiles that stage it)
   int amax_slot;       // snapshot index of kAbsMax
   float dt2;           // dt^2
   float csum;          // sum of the centre weights over the axes

@@ -132,3 +132,23 @@ def test_failed_allocations_leave_the_context_usable(fw):
     s.sync()
     s.close()
     assert rel_l2(g, pb.oracle_gradient(resid)) < TOL
+
+
+def test_tiling_arguments(fw):
+    """Tile indices and pipeline depths outside their ranges are refused
+    before any launch: every tile needs r + 2 stages except tile 9, whose
+    stages each hold one plane's reads and pipeline from two; the context then
+    runs at a valid tiling."""
+    ARG = 1
+    pb = _problem()
+    s = pb.solver(fw)
+    for bad in [(10, 0, 0), (-2, 0, 0), (9, 0, 1), (7, 0, 5), (4, 0, 1), (4, -1, 0)]:
+        with pytest.raises(fw.FdwError) as e:
+            s.set_tiling(*bad)
+        assert e.value.status == ARG, bad
+    s.set_tiling(9, 0, 2)
+    rec = s.forward(pb.q32)
+    s.sync()
+    assert s.tiling()["stages"] == 2
+    assert rel_l2(rec, pb.oracle_forward()) < TOL
+    s.close()

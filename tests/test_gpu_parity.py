@@ -44,23 +44,26 @@ def test_forward_3d_all_orders(fw, p):
 
 
 @pytest.mark.parametrize("p", [2, 4, 6, 8, 10, 12, 14, 16])
-@pytest.mark.parametrize("tile", [7, 8])
+@pytest.mark.parametrize("tile", [7, 8, 9])
 def test_forward_3d_tensor_memory_queue_all_orders(fw, p, tile):
-    """Tiles 7 and 8 keep the x queue in tensor memory: the same arithmetic as
-    tiles 4 and 6, so bit for bit their results, and the oracle's to 1e-4."""
+    """Tiles 7, 8 and 9 keep the x queue in tensor memory: the same arithmetic
+    as tiles 4, 6 and 4 (tile 9 forms two pair sums per instruction, each
+    rounded as the scalar add), so bit for bit their results, and the
+    oracle's to 1e-4."""
     pb = Problem((37, 45, 29), 10.0, p, 8, 70, nsrc=2, nrec=9, seed=p)
     rec, u = _fwd(fw, pb, tiling=(tile, 0, 0))
     ref, uref = pb.oracle_forward(final=True)
     assert_close(rec, ref, TOL, "traces")
     assert_close(u, uref, TOL, "wavefield")
-    rec4, u4 = _fwd(fw, pb, tiling=(tile - 3 if tile == 7 else 6, 0, 0))
+    rec4, u4 = _fwd(fw, pb, tiling=({7: 4, 8: 6, 9: 4}[tile], 0, 0))
     assert np.array_equal(rec, rec4) and np.array_equal(u, u4)
 
 
 @pytest.mark.parametrize("tiling", [(0, 0, 0), (1, 0, 0), (2, 0, 0), (4, 0, 0), (5, 0, 0),
                                     (0, 5, 0), (2, 3, 6), (1, 13, 0), (4, 64, 7), (0, 1, 0),
                                     (5, 7, 9), (6, 0, 0), (6, 9, 10), (7, 0, 0), (7, 1, 6),
-                                    (7, 13, 9), (8, 0, 0), (8, 9, 10)])
+                                    (7, 13, 9), (8, 0, 0), (8, 9, 10), (9, 0, 0), (9, 1, 2),
+                                    (9, 13, 3), (9, 9, 7), (9, 64, 5)])
 def test_forward_3d_tilings(fw, tiling):
     pb = Problem((40, 51, 35), 12.5, 8, 6, 60, nsrc=3, nrec=12, seed=11)
     rec, u = _fwd(fw, pb, tiling=tiling)
@@ -74,7 +77,7 @@ def test_tilings_agree_bitwise(fw):
     pb = Problem((30, 33, 41), 10.0, 8, 5, 50, nsrc=2, nrec=8, seed=5)
     base_rec, base_u = _fwd(fw, pb, tiling=(0, 0, 0))
     for t in [(1, 0, 0), (2, 7, 0), (0, 2, 6), (1, 64, 9), (4, 3, 0), (5, 11, 7), (6, 13, 8),
-              (7, 0, 0), (7, 5, 6), (8, 13, 8)]:
+              (7, 0, 0), (7, 5, 6), (8, 13, 8), (9, 0, 0), (9, 5, 2), (9, 13, 5)]:
         rec, u = _fwd(fw, pb, tiling=t)
         assert np.array_equal(rec, base_rec), t
         assert np.array_equal(u, base_u), t
@@ -101,9 +104,14 @@ def test_forward_ongrid_and_edge_points(fw):
 @pytest.mark.parametrize("mtype", ["f16", "bf16"])
 def test_forward_low_precision_model(fw, mtype):
     """The model stored in 16 bits (as s = 1/m): parity with the oracle run on
-    the same rounded model; the drift against the FP32 model is bounded."""
+    the same rounded model; the drift against the FP32 model is bounded.  The
+    16-bit model tiles change the stage layout, so tile 9 (centre tiles after
+    the model tile) must give tile 4's traces bit for bit."""
     pb = Problem((33, 30, 37), 12.5, 8, 6, 80, nsrc=1, nrec=8, seed=2)
     rec, _ = _fwd(fw, pb, mtype=mtype)
+    rec9, _ = _fwd(fw, pb, mtype=mtype, tiling=(9, 0, 3))
+    rec4, _ = _fwd(fw, pb, mtype=mtype, tiling=(4, 0, 0))
+    assert np.array_equal(rec9, rec4)
     mt = torch.float16 if mtype == "f16" else torch.bfloat16
     # the library stores s = 1/m in 16 bits
     s_rounded = torch.from_numpy(1.0 / pb.m32).to(mt).to(torch.float64).numpy()
@@ -143,7 +151,8 @@ def test_degenerate_cases(fw):
 
 
 @pytest.mark.parametrize("ndim,p,tiling", [(3, 4, None), (3, 8, None), (3, 16, None), (2, 8, None),
-                                           (3, 8, (7, 0, 0)), (3, 16, (8, 0, 0))])
+                                           (3, 8, (7, 0, 0)), (3, 16, (8, 0, 0)),
+                                           (3, 8, (9, 0, 0)), (3, 12, (9, 7, 3))])
 def test_adjoint_parity_and_dot_test(fw, ndim, p, tiling):
     shape = (31, 27, 35) if ndim == 3 else (50, 45)
     pb = Problem(shape, 10.0, p, 6, 70, nsrc=2, nrec=7, seed=21 + p)
@@ -162,7 +171,7 @@ def test_adjoint_parity_and_dot_test(fw, ndim, p, tiling):
 
 
 @pytest.mark.parametrize("k,tiling", [(1, None), (4, None), (9, None), (70, None), (4, (7, 0, 0)),
-                                      (9, (8, 11, 0))])
+                                      (9, (8, 11, 0)), (4, (9, 0, 0)), (9, (9, 11, 3))])
 def test_gradient_fp32_checkpoints(fw, k, tiling):
     pb = Problem((29, 26, 31), 10.0, 8, 6, 70, nsrc=1, nrec=8, seed=31)
     rng = np.random.default_rng(3)
@@ -327,7 +336,7 @@ def full_grid_case():
 # (the last case runs every step in one persistent launch)
 @pytest.mark.parametrize("tiling,persist", [(None, False), ((4, 80, 7), False),
                                             ((4, 64, 7), False), ((7, 80, 7), False),
-                                            ((4, 80, 7), True)])
+                                            ((4, 80, 7), True), ((9, 128, 5), True)])
 def test_config_3d_256_so8_full_grid_first_steps(fw, full_grid_case, tiling, persist):
     w, q32, ref, uref = full_grid_case
     dev = torch.device("cuda", 0)

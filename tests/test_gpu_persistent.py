@@ -46,7 +46,8 @@ def test_persistent_equals_per_step_all_orders(fw, p):
 
 
 @pytest.mark.parametrize("tiling", [(0, 0, 0), (4, 8, 0), (4, 13, 7), (6, 9, 10), (7, 11, 0),
-                                    (8, 0, 0), (1, 0, 0), (5, 7, 9)])
+                                    (8, 0, 0), (1, 0, 0), (5, 7, 9), (9, 0, 0), (9, 11, 3),
+                                    (9, 5, 2)])
 def test_persistent_equals_per_step_tilings(fw, tiling):
     """Short x chunks give many rows, so units of a later step run while the
     previous step is still in progress elsewhere in the grid."""
