@@ -219,9 +219,10 @@ fdw_status fdw_set_checkpoint_budget(fdw_ctx* ctx, int max_pairs);
  * nslots < 0, cap < 0 or actions NULL with cap > 0.  Host only. */
 int fdw_checkpoint_schedule(int nseg, int nslots, int* actions, int cap);
 
-/* Force a tile configuration: tile index (0..9, -1 = default; 3 is meant for
- * 2D grids, 6 keeps per-plane tiles in a second ring, 7 and 8 are 4 and 6
- * with the x-direction queue in tensor memory, 9 is 7 with each pipeline
+/* Force a tile configuration: tile index (0..9, -1 = default: 9 on 3D grids,
+ * 3 on 2D grids; 3 is meant for 2D grids, 6 keeps per-plane tiles in a
+ * second ring, 7 and 8 are 4 and 6 with the x-direction queue in tensor
+ * memory, 9 is 7 with each pipeline
  * stage holding exactly one plane's reads: the halo plane x, its tiles and
  * the centre tile of plane x + r), x-chunk length (0 = default) and pipeline
  * depth of the forward and adjoint steps (>= r + 2 with r = space_order / 2,

@@ -537,11 +537,14 @@ static void choose_default_tiling(Plan& pl) {
   bool all2d = true;
   for (auto* c : pl.shots)
     if (c->ny > 1) all2d = false;
-  // tile 4 (16 x 32 points, four consumer warps, 96 registers: four CTAs per
-  // SM) measured fastest or within noise of it on every 3D case tried
-  pl.tile = pl.tile_req >= 0 ? pl.tile_req : (all2d ? 3 : 4);
+  // tile 9 (16 x 32 points, four consumer warps, the x queue in tensor
+  // memory, one plane's reads per stage) measured fastest on the 3D cases
+  // tried at space orders 4 to 16 and faster than the previous default
+  // (tile 4) at order 2; four stages up to radius 4, five above
+  pl.tile = pl.tile_req >= 0 ? pl.tile_req : (all2d ? 3 : 9);
   const int ms = max_stages(pl, pl.tile);
-  pl.stages = pl.stages_req > 0 ? std::min(pl.stages_req, ms) : std::min(pl.r + 4, ms);
+  const int st_def = kTiles[pl.tile].ca ? (pl.r > 4 ? 5 : 4) : pl.r + 4;
+  pl.stages = pl.stages_req > 0 ? std::min(pl.stages_req, ms) : std::min(st_def, ms);
   if (pl.stages < min_stages(pl.r, pl.tile, false))
     fail(FDW_ERR_ARG, "pipeline too shallow for this order");
   if (pl.lx_req > 0) {
@@ -549,8 +552,12 @@ static void choose_default_tiling(Plan& pl) {
     return;
   }
   // x chunks of 32 planes (the 2r warm-up planes of a chunk stay a minor
-  // share), halved while the grid gives fewer than two units per resident CTA
+  // share), halved while the grid gives fewer than two units per resident
+  // CTA; with tile 9, chunks of 128 planes, halved while there are fewer
+  // units than resident CTAs (its stages are short, and longer chunks
+  // measured faster)
   const int slots = resident_ctas(pl, pl.tile, pl.stages, false);
+  const bool ca = kTiles[pl.tile].ca;
   const int TY = tile_rows(kTiles[pl.tile]);
   long long cols = 0;
   int nxmax = 1;
@@ -558,8 +565,8 @@ static void choose_default_tiling(Plan& pl) {
     cols += (long long)((c->ny + TY - 1) / TY) * ((c->nz + kTZ - 1) / kTZ);
     nxmax = std::max(nxmax, c->nx);
   }
-  int lx = std::min(32, nxmax);
-  while (lx > 8 && cols * ((nxmax + lx - 1) / lx) < 2LL * slots) lx /= 2;
+  int lx = std::min(ca ? 128 : 32, nxmax);
+  while (lx > 8 && cols * ((nxmax + lx - 1) / lx) < (ca ? 1LL : 2LL) * slots) lx /= 2;
   pl.lx = std::max(1, lx);
 }
 
@@ -1926,7 +1933,7 @@ static void plan_autotune(Plan& pl, int steps) {
     }
     std::vector<int> tiles =
         all2d ? std::vector<int>{3} : std::vector<int>{0, 1, 2, 4, 5, 6, 7, 8, 9};
-    std::vector<int> lxs = {16, 32, 48, 64, 80, 96, 128, nxmax};
+    std::vector<int> lxs = {16, 32, 48, 64, 80, 96, 128, 160, 192, 256, nxmax};
     cudaStream_t s = pl.cap;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -2003,11 +2010,11 @@ static void plan_autotune(Plan& pl, int steps) {
     for (int t : tiles) {
       const int ms = max_stages(pl, t);
       // r + 2 .. r + 4 stages; a tile whose stages hold one plane's reads
-      // (ca) pipelines from two: 3, 5 and 7 stages (4, 5, 6 above radius 4,
+      // (ca) pipelines from two: 3, 4 and 5 stages (4, 5, 6 above radius 4,
       // where three of its CTAs fit on an SM with up to six)
       std::vector<int> sts;
       for (int extra : {1, 2, 3})
-        sts.push_back(std::min(kTiles[t].ca ? (pl.r > 4 ? 3 + extra : 1 + 2 * extra)
+        sts.push_back(std::min(kTiles[t].ca ? (pl.r > 4 ? 3 + extra : 2 + extra)
                                             : pl.r + 1 + extra, ms));
       sts.erase(std::unique(sts.begin(), sts.end()), sts.end());
       for (int st : sts) {
