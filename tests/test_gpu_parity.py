@@ -331,12 +331,14 @@ def full_grid_case():
     return w, q, ref, uref
 
 
-# the autotuner's choice (as in the bench) and the tilings the bench's tuner
-# has picked on the GB300 (tile 4 with x chunks of 80 and 64, 7 stages)
-# (the last case runs every step in one persistent launch)
+# the autotuner's choice (as in the bench) and tilings the bench's tuner has
+# picked on the GB300 (tile 4 with x chunks of 80 and 64, 7 stages; tile 9
+# with x chunks of 128 or 192, 5 stages); the persist cases run every step
+# in one persistent launch
 @pytest.mark.parametrize("tiling,persist", [(None, False), ((4, 80, 7), False),
                                             ((4, 64, 7), False), ((7, 80, 7), False),
-                                            ((4, 80, 7), True), ((9, 128, 5), True)])
+                                            ((4, 80, 7), True), ((9, 128, 5), True),
+                                            ((9, 192, 5), True)])
 def test_config_3d_256_so8_full_grid_first_steps(fw, full_grid_case, tiling, persist):
     w, q32, ref, uref = full_grid_case
     dev = torch.device("cuda", 0)
