@@ -1496,9 +1496,21 @@ static void adjoint_body(Plan& pl, cudaStream_t s) {
   int flags = 0;
   if (pl.max_rec > 0) flags |= kInject;
   if (pl.max_src > 0) flags |= kSample;
-  for (int k = nt - 1; k >= 1; --k) {
-    StepArgs a{kRoleAdj, (k + 1) & 1, k & 1, k & 1, 0, k, k, flags, false};
-    launch_adjoint_step(pl, a, s);
+  if (plan_persistent(pl)) {
+    // every adjoint step in one launch, time running backwards; the receiver
+    // data are injected at the unit tails (spread over the units of every row)
+    CK(cudaMemsetAsync(pl.d_row_done, 0, sizeof(int) * pl.nrows, s));
+    if (nt > 1) {
+      StepArgs a{kRoleAdj, 0, 1, 1, 0, nt - 1, nt - 1, flags | kPersist | kReverse, false};
+      a.step0 = 0;
+      a.step_end = nt - 1;
+      launch_step(pl, a, s);
+    }
+  } else {
+    for (int k = nt - 1; k >= 1; --k) {
+      StepArgs a{kRoleAdj, (k + 1) & 1, k & 1, k & 1, 0, k, k, flags, false};
+      launch_adjoint_step(pl, a, s);
+    }
   }
   if (pl.max_src > 0)
     CK(launch_sample(pl.d_desc[kRoleAdj], (int)pl.shots.size(), pl.max_src, 1, 0, s));
@@ -2307,7 +2319,8 @@ fdw_status fdw_adjoint(fdw_ctx* c, const float* d, float* qadj, void* stream) {
     float* qo = device_out(c, 9, qadj, nq, &host);
     pl.hdesc[kRoleAdj][0].smp_out = qo;
     upload_desc(pl, kRoleAdj, s);
-    run_graph(pl, "adj", s, [&](cudaStream_t st) { adjoint_body(pl, st); });
+    run_graph(pl, plan_persistent(pl) ? "adj ps" : "adj", s,
+              [&](cudaStream_t st) { adjoint_body(pl, st); });
     if (host) CK(cudaMemcpyAsync(qadj, qo, nq * sizeof(float), cudaMemcpyDeviceToHost, s));
     c->adj_done = true;
   });

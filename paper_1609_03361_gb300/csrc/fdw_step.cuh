@@ -144,14 +144,21 @@ struct Lanes {
 
 // Wavefield slots and time rows of the step a unit belongs to (one step per
 // launch: the launch's; kPersist: the unit's own step n, with u^n in slot
-// n & 1 and u^{n+1} written over u^{n-1} in slot (n + 1) & 1).
+// n & 1 and u^{n+1} written over u^{n-1} in slot (n + 1) & 1; with kReverse
+// the adjoint step at time t = inj_row - n).
 struct StepCtx {
   int cur, prev, out;
   int inj_row, smp_row;
 };
 
 __device__ __forceinline__ StepCtx step_ctx(const StepParams& P, int n) {
-  if (P.flags & kPersist) return StepCtx{n & 1, (n + 1) & 1, (n + 1) & 1, n, n};
+  if (P.flags & kPersist) {
+    if (P.flags & kReverse) {  // adjoint step at time t: lambda^{t+1} in slot (t+1) & 1,
+      const int t = P.inj_row - n;  // lambda^t written over lambda^{t+2} in slot t & 1
+      return StepCtx{(t + 1) & 1, t & 1, t & 1, t, t};
+    }
+    return StepCtx{n & 1, (n + 1) & 1, (n + 1) & 1, n, n};
+  }
   return StepCtx{P.cur, P.prev, P.out, P.inj_row, P.smp_row};
 }
 

@@ -124,3 +124,44 @@ def test_persistent_rejected_on_slabs(fw):
         s.set_persistent(True)
     assert e.value.status == 9
     s.close()
+
+
+def _adj(fw, pb, d, persist, tiling=None):
+    s = pb.solver(fw, tiling=tiling)
+    s.set_persistent(persist)
+    qa = s.adjoint(d)
+    s.sync()
+    s.close()
+    return qa
+
+
+@pytest.mark.parametrize("p,tiling", [(2, None), (4, None), (8, None), (12, None), (16, None),
+                                      (8, (9, 5, 2)), (8, (7, 11, 0)), (8, (4, 8, 0)),
+                                      (8, (0, 13, 0))])
+def test_persistent_adjoint_equals_per_step(fw, p, tiling):
+    """The adjoint as one persistent launch (time running backwards, the
+    receiver data injected at the unit tails) gives the per-step loop's
+    source-side traces bit for bit (the per-step loop injects in a launch of
+    its own, with the same arithmetic), the oracle's to 1e-4, and closes the
+    dot test against the persistent forward run."""
+    pb = Problem((33, 29, 37), 10.0, p, 6, 60, nsrc=2, nrec=9, seed=300 + p)
+    rng = np.random.default_rng(p)
+    d = rng.standard_normal((pb.nt, 9)).astype(np.float32)
+    qa1 = _adj(fw, pb, d, False, tiling)
+    qa2 = _adj(fw, pb, d, True, tiling)
+    assert np.array_equal(qa1, qa2)
+    assert_close(qa2, pb.oracle_adjoint(d), TOL, "adjoint traces")
+    rec, _ = _fwd(fw, pb, True, tiling)
+    lhs = float(np.sum(rec.astype(np.float64) * d))
+    rhs = float(np.sum(pb.q32.astype(np.float64) * qa2))
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs))
+
+
+def test_persistent_adjoint_2d_and_short_runs(fw):
+    pb = Problem((61, 57), 10.0, 4, 20, 120, nsrc=1, nrec=11, seed=8)
+    d = np.random.default_rng(8).standard_normal((pb.nt, 11)).astype(np.float32)
+    assert np.array_equal(_adj(fw, pb, d, False), _adj(fw, pb, d, True))
+    for nt in (1, 2, 3):
+        pb = Problem((20, 21, 22), 10.0, 8, 3, nt, nsrc=1, nrec=3, seed=nt)
+        d = np.random.default_rng(nt).standard_normal((nt, 3)).astype(np.float32)
+        assert np.array_equal(_adj(fw, pb, d, False), _adj(fw, pb, d, True))
