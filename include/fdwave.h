@@ -235,15 +235,20 @@ fdw_status fdw_set_tiling(fdw_ctx* ctx, int tile, int xchunk, int stages);
 /* Run plain forward modelling (fdw_forward, and fdw_batch_forward when every
  * context of the batch asks for it) and the plain adjoint (fdw_adjoint) as one
  * persistent launch over all time steps (on = 1, the default) or as one
- * launch per step (on = 0).  The schemes of Sec. 5 (Eq. 3) and Sec. 5.1 are
+ * launch per step (on = 0).  With on = 1 the checkpointed forward
+ * (fdw_forward_ckpt without a checkpoint budget) runs one persistent launch
+ * per segment of ckpt_every steps, each followed by the storing of its
+ * snapshot pair, and the gradient recomputes each segment in one launch; the
+ * gradient's adjoint steps, and every step under a checkpoint budget, keep
+ * one launch per step.  The schemes of Sec. 5 (Eq. 3) and Sec. 5.1 are
  * unchanged, and so are the results, bit for bit: the launch takes work units
  * step by step, and a unit of step n + 1 starts as soon as every unit that
  * updated the planes it reads (its own x chunk and the neighbouring ones, all
  * column tiles) has finished step n, instead of after the whole step; the
  * paper has no counterpart (it is a scheduling change of the same time loop).
- * Checkpointed forward runs and the gradient keep one launch per step, and so
- * do slab contexts (which never run whole time loops).  The autotuner times
- * the mode the context is in.  FDW_ERR_STATE for on = 1 on a slab context. */
+ * Slab contexts (which never run whole time loops) step one launch at a time.
+ * The autotuner times the mode the context is in.  FDW_ERR_STATE for on = 1
+ * on a slab context. */
 fdw_status fdw_set_persistent(fdw_ctx* ctx, int on);
 
 /* Tile configuration in use: out[0] = tile index, out[1] = x-chunk length,

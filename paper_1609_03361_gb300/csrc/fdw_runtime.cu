@@ -1141,6 +1141,36 @@ static void forward_body(Plan& pl, int k, int stype, cudaStream_t s) {
                        s));
     return;
   }
+  if (k > 0 && !rv && plan_persistent(pl)) {
+    // checkpointed forward: one persistent launch per segment of k steps,
+    // each ending where snapshot pair j = (u^{jk}, u^{jk-1}) is complete and
+    // the pair is stored; with the fused maximum, the segment's last two
+    // steps (those that make u^{jk-1} and u^{jk}) fold it into amax[j-1]
+    for (int n0 = 0; n0 + 1 < nt;) {
+      const int j = n0 / k + 1;
+      const int n1 = std::min(j * k, nt - 1);  // steps n0 .. n1-1
+      const bool pair = n1 == j * k && j <= nsnap;
+      CK(cudaMemsetAsync(pl.d_row_done, 0, sizeof(int) * pl.nrows, s));
+      StepArgs a{kRoleFwd, 0, 1, 1, 0, n0, 0, flags_base | kPersist, false};
+      if (pair && fused_max) {
+        a.flags |= kAbsMax;
+        a.amax_slot = j - 1;
+      }
+      a.step0 = 0;
+      a.step_end = n1 - n0;
+      launch_step(pl, a, s);
+      if (pair) {
+        if (scaled && !fused_max)
+          CK(launch_absmax(pl.d_pack + (size_t)(j - 1) * ns, (int)ns, pl.max_slot, s));
+        CK(launch_pack(pl.d_pack + (size_t)(j - 1) * ns, (int)ns, pl.max_slot, stype, s));
+      }
+      n0 = n1;
+    }
+    if (pl.max_rec > 0)
+      CK(launch_sample(pl.d_desc[kRoleFwd], (int)pl.shots.size(), pl.max_rec, (nt - 1) & 1, nt - 1,
+                       s));
+    return;
+  }
   for (int n = 0; n + 1 < nt; ++n) {
     StepArgs a{kRoleFwd, n & 1, (n + 1) & 1, (n + 1) & 1, 0, n, n, flags_base, false};
     if (fused_max) {
@@ -1527,6 +1557,7 @@ static void gradient_body(Plan& pl, int k, int stype, bool diff, cudaStream_t s)
   const int adj_flags = (pl.max_rec > 0 ? kInject : 0) | (diff ? kInjectDiff : 0);
   const int rec_flags = pl.max_src > 0 ? kInject : 0;
   const int nseg = (nt + k - 1) / k;
+  const bool persist = plan_persistent(pl);
   for (int j = nseg - 1; j >= 0; --j) {
     const int a0 = j * k, b0 = std::min((j + 1) * k, nt);
     if (j == 0) {
@@ -1535,12 +1566,28 @@ static void gradient_body(Plan& pl, int k, int stype, bool diff, cudaStream_t s)
       CK(launch_unpack(pl.d_unpack + (size_t)(j - 1) * ns, (int)ns, pl.max_slot, stype, s));
     }
     // recompute u^{a0+1} .. u^{b0-1}; slot i holds u^{a0-1+i}
-    for (int n = a0; n <= b0 - 2; ++n) {
-      StepArgs a{kRoleRec, n - a0 + 1, n - a0, n - a0 + 2, 0, n, 0, rec_flags, false};
-      launch_step(pl, a, s);
+    const int lo = std::max(a0, 1);
+    if (persist) {
+      // the segment's recompute steps as one persistent launch
+      if (b0 - 1 > a0) {
+        CK(cudaMemsetAsync(pl.d_row_done, 0, sizeof(int) * pl.nrows, s));
+        StepArgs a{kRoleRec, 1, 0, 2, 0, a0, 0, rec_flags | kPersist | kLinear, false};
+        a.step0 = 0;
+        a.step_end = b0 - 1 - a0;
+        launch_step(pl, a, s);
+      }
+    } else {
+      for (int n = a0; n <= b0 - 2; ++n) {
+        StepArgs a{kRoleRec, n - a0 + 1, n - a0, n - a0 + 2, 0, n, 0, rec_flags, false};
+        launch_step(pl, a, s);
+      }
     }
-    // adjoint steps with the imaging condition
-    for (int kk = b0 - 1; kk >= std::max(a0, 1); --kk) {
+    // adjoint steps with the imaging condition, one launch each: the
+    // residuals of thousands of receivers are injected by a launch of their
+    // own over all SMs (at the unit tails of a persistent launch the few
+    // units that hold them gate their rows' next steps: measured slower with
+    // four shots per batch)
+    for (int kk = b0 - 1; kk >= lo; --kk) {
       StepArgs a{kRoleAdj, (kk + 1) & 1, kk & 1, kk & 1, kk - a0 + 1, kk, 0, adj_flags, true};
       launch_adjoint_step(pl, a, s);
     }
@@ -1817,7 +1864,7 @@ static void plan_forward(Plan& pl, const float* const* q, float* const* rec, int
   std::ostringstream key;
   key << "fwd k" << k << " t" << stype << " rv" << (k > 0 && pl.shots[0]->revolve ? pl.shots[0]->nsnap : 0);
   if (tb) key << " tb";
-  if (k == 0 && !tb && plan_persistent(pl)) key << " ps";
+  if (!tb && plan_persistent(pl)) key << " ps";
   run_graph(pl, key.str(), s, [&](cudaStream_t st) {
     if (tb) tb_forward_body(pl, st);
     else forward_body(pl, k, stype, st);
@@ -1861,6 +1908,7 @@ static void plan_gradient(Plan& pl, const float* const* resid, const float* cons
   const bool rv = pl.shots[0]->revolve;
   std::ostringstream key;
   key << "grad k" << k << " t" << stype << " d" << diff << " rv" << (rv ? pl.shots[0]->nsnap : 0);
+  if (plan_persistent(pl)) key << " ps";
   run_graph(pl, key.str(), s, [&](cudaStream_t st) {
     if (rv) revolve_gradient_body(pl, k, stype, diff, st);
     else gradient_body(pl, k, stype, diff, st);

@@ -142,24 +142,32 @@ struct Lanes {
   int zl;  // local z of the thread's first point (multiple of 4)
 };
 
-// Wavefield slots and time rows of the step a unit belongs to (one step per
-// launch: the launch's; kPersist: the unit's own step n, with u^n in slot
-// n & 1 and u^{n+1} written over u^{n-1} in slot (n + 1) & 1; with kReverse
-// the adjoint step at time t = inj_row - n).
+// Wavefield slots, time rows and snapshot-maximum flag of the step a unit
+// belongs to.  One step per launch: the launch's.  kPersist: the unit's own
+// step n of the launch, at time t = inj_row + n with u^t in slot t & 1 and
+// u^{t+1} written over u^{t-1} in slot (t + 1) & 1, the snapshot maximum
+// (kAbsMax) folded on the launch's last two steps; with kReverse the adjoint
+// step at time t = inj_row - n (lambda^{t+1} in slot (t + 1) & 1, lambda^t
+// written over lambda^{t+2} in slot t & 1); with kLinear slots n + 1, n and
+// n + 2 (the recompute buffer).
 struct StepCtx {
   int cur, prev, out;
   int inj_row, smp_row;
+  bool amx;
 };
 
 __device__ __forceinline__ StepCtx step_ctx(const StepParams& P, int n) {
   if (P.flags & kPersist) {
-    if (P.flags & kReverse) {  // adjoint step at time t: lambda^{t+1} in slot (t+1) & 1,
-      const int t = P.inj_row - n;  // lambda^t written over lambda^{t+2} in slot t & 1
-      return StepCtx{(t + 1) & 1, t & 1, t & 1, t, t};
+    if (P.flags & kReverse) {
+      const int t = P.inj_row - n;
+      return StepCtx{(t + 1) & 1, t & 1, t & 1, t, t, false};
     }
-    return StepCtx{n & 1, (n + 1) & 1, (n + 1) & 1, n, n};
+    const int t = P.inj_row + n;
+    const bool amx = (P.flags & kAbsMax) != 0 && n >= P.step_end - 2;
+    if (P.flags & kLinear) return StepCtx{n + 1, n, n + 2, t, P.smp_row, amx};
+    return StepCtx{t & 1, (t + 1) & 1, (t + 1) & 1, t, t, amx};
   }
-  return StepCtx{P.cur, P.prev, P.out, P.inj_row, P.smp_row};
+  return StepCtx{P.cur, P.prev, P.out, P.inj_row, P.smp_row, (P.flags & kAbsMax) != 0};
 }
 
 // kPersist: wait (bounded) until every unit of the rows that a unit of `row`
@@ -237,7 +245,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
   const int S = P.stages;
   const int ny = d->ny, nz = d->nz, nzp = d->nzp;
   const bool etaf = (P.flags & kEtaField) != 0;
-  const bool amx = (P.flags & kAbsMax) != 0;
+  const bool amx = sc.amx;
   const int r0 = L.r0, zl = L.zl;
   const int z = un.z0 + zl;
   const bool zin = z < nz;
@@ -781,6 +789,9 @@ step_kernel(const __grid_constant__ StepParams P) {
       const StepCtx sc = step_ctx(P, s_step[ca.stage]);
       const ShotDesc* d = P.shots + un.shot;
       const int mtype = d->mtype;
+      // the maximum covers this unit alone (a persistent launch mixes units
+      // of steps that fold it with units of steps that do not)
+      tmax = 0.f;
       if (mtype == kF16)
         ok = run_unit<R, NY, BY, GRAD, XU, SPLIT, TQ, CA, __half>(P, un, d, u, smem, full0, empty0, ca, cb, csmem, cfull0, cempty0, cc,
                                                abort_flag, lane, L, tmax, tq, sc);
@@ -858,7 +869,7 @@ step_kernel(const __grid_constant__ StepParams P) {
           }
         }
       }
-      if (P.flags & kAbsMax) {
+      if (sc.amx) {
         // the unit's maximum after injection (an injected node also counted
         // its value before injection: an upper bound, which is all the
         // snapshot scale needs)

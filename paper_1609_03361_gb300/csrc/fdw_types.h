@@ -30,13 +30,15 @@ enum StepFlags : int {
   kTestStall = 16,   // test hook: the producer issues no loads, so every consumer
                      // wait runs out of its clock budget and reports an error
   kAbsMax = 32,      // fold max |u^{n+1}| of every unit into amax[amax_slot] of its shot
-  kPersist = 64,     // forward and adjoint roles: one launch runs the steps
+  kPersist = 64,     // forward, recompute and adjoint roles: one launch runs the steps
                      // [step0, step_end); tickets run over (step, unit), step by
                      // step, and a unit of step n + 1 starts once the rows of units
                      // it reads have finished step n (row_done counts finished
                      // units per row)
   kReverse = 128,    // with kPersist: step n of the launch is the adjoint step at
                      // time t = inj_row - n (time runs backwards)
+  kLinear = 256,     // with kPersist: step n reads slots n + 1 (u^t) and n (u^{t-1})
+                     // and writes slot n + 2, t = inj_row + n (recompute buffers)
 };
 
 // Per-shot description; lives in device memory, 128-byte aligned (tensor maps).
