@@ -1993,7 +1993,12 @@ static void plan_autotune(Plan& pl, int steps) {
     }
     std::vector<int> tiles =
         all2d ? std::vector<int>{3} : std::vector<int>{0, 1, 2, 4, 5, 6, 7, 8, 9};
-    std::vector<int> lxs = {16, 32, 48, 64, 80, 96, 128, 160, 192, 256, nxmax};
+    // (half and whole columns as well: with one persistent launch over the
+    // steps, the high orders measured fastest with one or two chunks per
+    // column, which halve the 2r warm-up planes per update)
+    std::vector<int> lxs = {16, 32, 48, 64, 80, 96, 128, 160, 192, 256, (nxmax + 1) / 2, nxmax};
+    std::sort(lxs.begin(), lxs.end());
+    lxs.erase(std::unique(lxs.begin(), lxs.end()), lxs.end());
     cudaStream_t s = pl.cap;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
