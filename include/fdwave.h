@@ -226,8 +226,7 @@ int fdw_checkpoint_schedule(int nseg, int nslots, int* actions, int cap);
  * stage holding exactly one plane's reads: the halo plane x, its tiles and
  * the centre tile of plane x + r), x-chunk length (0 = default) and pipeline
  * depth of the forward and adjoint steps (>= r + 2 with r = space_order / 2,
- * >= 2 for tile 9, 0 = default; the gradient step picks its own and runs
- * tile 9 as tile 7).  Every tile computes each point with the same arithmetic,
+ * >= 2 for tile 9, 0 = default; the gradient step picks its own).  Every tile computes each point with the same arithmetic,
  * so the results do not depend on the tiling, bit for bit.  FDW_ERR_ARG
  * outside these ranges. */
 fdw_status fdw_set_tiling(fdw_ctx* ctx, int tile, int xchunk, int stages);

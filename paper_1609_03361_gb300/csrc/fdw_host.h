@@ -268,7 +268,9 @@ inline int second_ring_stages(const StageLayout& L, int stages) {
 }
 
 inline StageLayout stage_layout(int r, int tile, int mt_bytes, bool grad, bool etaf) {
-  const bool split = grad || kTiles[tile].split;
+  // the gradient step's tiles go to the second ring, except in tiles whose
+  // stages hold one plane's reads (ca), where they are part of that plane
+  const bool split = (grad && !kTiles[tile].ca) || kTiles[tile].split;
   const int TY = tile_rows(kTiles[tile]);
   const int R4 = (r + 3) & ~3;
   const int ZW = kTZ + 2 * R4, YW = TY + 2 * r;
@@ -300,7 +302,8 @@ inline StageLayout stage_layout(int r, int tile, int mt_bytes, bool grad, bool e
 // until x is updated while planes up to x + r are read ahead, unless the
 // centre values come in tiles of their own (then any two stages pipeline).
 inline int min_stages(int r, int tile, bool grad) {
-  return (!grad && kTiles[tile].ca) ? 2 : r + 2;
+  (void)grad;
+  return kTiles[tile].ca ? 2 : r + 2;
 }
 
 // Dynamic shared memory of a launch: the stages of both rings, their full

@@ -22,7 +22,8 @@ namespace fdw {
 // x + r (the values that join the x queue), so every stage is freed after one
 // plane instead of staying r + 1 planes, and a few stages pipeline; it also
 // forms the neighbour pair sums two at a time (fewer registers), so at the
-// high orders more CTAs fit on an SM (the gradient step runs as tile 7).
+// high orders more CTAs fit on an SM.  Its gradient step stages the forward
+// field and accumulator tiles of plane x in the same stage.
 struct TileShape {
   int ny_pts;
   int warps;

@@ -900,8 +900,9 @@ static int grad_stages(Plan& pl) {
   const void* fn = step_fn(pl.r, pl.tile, true);
   const int threads = (kTiles[pl.tile].warps + 1) * 32;
   const int cap = device_smem_optin(pl.device) - 1024;
-  int best = pl.r + 2, best_nb = -1;
-  for (int st = pl.r + 2; st <= 2 * pl.r + 8 && (int)smem_bytes(L, st) <= cap; ++st) {
+  const int lo = min_stages(pl.r, pl.tile, true);
+  int best = lo, best_nb = -1;
+  for (int st = lo; st <= 2 * pl.r + 8 && (int)smem_bytes(L, st) <= cap; ++st) {
     const size_t smem = launch_smem(pl, pl.tile, L, st, fn, threads);
     const int nb = occupancy(pl, pl.tile, fn, threads, smem);
     if (nb >= best_nb) {

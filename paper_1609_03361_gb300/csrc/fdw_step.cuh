@@ -235,7 +235,7 @@ __device__ __forceinline__ bool run_unit(const StepParams& P, const Unit& un, co
                                          volatile int* abort_flag, int lane, const Lanes L,
                                          float& tmax, uint32_t tq, const StepCtx sc) {
   static_assert(!TQ || (NY == 1 && !XU), "the tensor-memory queue holds one row per thread");
-  static_assert(!CA || (TQ && !SPLIT && !GRAD), "centre tiles are staged for the tensor-memory queue");
+  static_assert(!CA || (TQ && !SPLIT), "centre tiles are staged for the tensor-memory queue");
   constexpr int TZ = kTZ;
   constexpr int R4 = Halo<R>::R4;
   constexpr int ZW = Halo<R>::ZW;
@@ -565,7 +565,7 @@ template <int R, int NY, int BY, bool GRAD, bool XU, bool SPLIT = GRAD, bool TQ 
 __global__ void __launch_bounds__((BY + 1) * 32, (SPLIT && !GRAD && R >= 7 && !TQ) ? 3 : 0)
 step_kernel(const __grid_constant__ StepParams P) {
   static_assert(!TQ || BY == 4, "the tensor-memory queue maps the four consumer warps to the four lane quarters");
-  static_assert(!CA || (TQ && !SPLIT && !GRAD), "centre tiles are staged for the tensor-memory queue");
+  static_assert(!CA || (TQ && !SPLIT), "centre tiles are staged for the tensor-memory queue");
   constexpr int TZ = kTZ;
   constexpr int TY = 4 * BY * NY;
   constexpr int R4 = Halo<R>::R4;
@@ -690,6 +690,10 @@ step_kernel(const __grid_constant__ StepParams P) {
               tma_load_4d(sb, &d->tm_uh, un.z0 - R4, un.y0 - R, x, sc.cur, full);
               tma_load_4d(sb + P.off_p, &d->tm_uc, un.z0, un.y0, x, sc.prev, full);
               tma_load_3d(sb + P.off_m, &d->tm_m, un.z0, un.y0, x, full);
+              if (GRAD) {
+                tma_load_4d(sb + P.off_f, &d->tm_f, un.z0, un.y0, x, P.fslot, full);
+                tma_load_3d(sb + P.off_a, &d->tm_a, un.z0, un.y0, x, full);
+              }
               if (P.flags & kEtaField) tma_load_3d(sb + P.off_e, &d->tm_e, un.z0, un.y0, x, full);
             }
             ++issued;

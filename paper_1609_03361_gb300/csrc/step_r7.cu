@@ -24,7 +24,7 @@ const void* step_kernel_r7(int tile, bool grad) {
                           : (const void*)&step_kernel<7, 1, 4, false, false, false, true>;
     case 8: return grad ? (const void*)&step_kernel<7, 1, 4, true, false, true, true>
                           : (const void*)&step_kernel<7, 1, 4, false, false, true, true>;
-    case 9: return grad ? (const void*)&step_kernel<7, 1, 4, true, false, true, true>
+    case 9: return grad ? (const void*)&step_kernel<7, 1, 4, true, false, false, true, true>
                           : (const void*)&step_kernel<7, 1, 4, false, false, false, true, true>;
     default: return nullptr;
   }

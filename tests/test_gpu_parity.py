@@ -447,3 +447,23 @@ def test_config_3d_512_so16_full_grid_first_steps(fw):
                                w.rec, final=True)
     assert_close(u, uref, TOL, "wavefield")
     assert_close(rec, ref, TOL, "traces")
+
+
+@pytest.mark.parametrize("p,k,stype", [(4, 5, "f32"), (8, 10, "f32"), (8, 7, "f16"), (12, 4, "f32"),
+                                       (16, 9, "f16")])
+def test_gradient_tile9_equals_tile4(fw, p, k, stype):
+    """Tile 9's gradient step stages the forward-field and accumulator tiles
+    with the plane's other reads and forms the pair sums two at a time: the
+    arithmetic of tile 4's gradient step, so its gradient bit for bit."""
+    pb = Problem((29, 26, 31), 10.0, p, 6, 60, nsrc=1, nrec=8, seed=500 + p)
+    resid = np.random.default_rng(p).standard_normal((pb.nt, 8)).astype(np.float32)
+    out = []
+    for tiling in [(4, 0, 0), (9, 0, 0), (9, 5, 2)]:
+        s = pb.solver(fw, tiling=tiling)
+        s.forward_ckpt(pb.q32, k, stype)
+        out.append(s.gradient(resid))
+        s.sync()
+        s.close()
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    if stype == "f32":
+        assert rel_l2(out[1], pb.oracle_gradient(resid)) < TOL
