@@ -843,14 +843,25 @@ def precision_measure(dev):
     s.set_receivers(w.rec)
     qd = torch.from_numpy(w.wavelet().astype(np.float32)[:, None]).to(dev)
     md = torch.from_numpy(w.m.astype(np.float32)).to(dev)
-    tr = {}
+    tr, gp = {}, {}
+    pts = int(np.prod(w.comp_shape))
     for mt in ("f32", "f16", "bf16"):
         s.set_model(md, "physical", mt)
         tr[mt] = s.forward(qd).cpu().numpy()
+        # the same run again, timed (16 B of algorithmic traffic per point
+        # with the FP32 model, 14 B with a 16-bit one)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.forward(qd)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        gp[mt] = pts * (w.nt - 1) / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    tiling = s.tiling()
     s.close()
     out["model_storage_full_grid_vs_fp32"] = {
         "workload": "512^3 (592^3 computational) SO16, 2000 steps, 16384 receivers",
-        "rel_l2_traces": {mt: rel(tr[mt], tr["f32"]) for mt in ("f16", "bf16")}}
+        "rel_l2_traces": {mt: rel(tr[mt], tr["f32"]) for mt in ("f16", "bf16")},
+        "gpts": gp, "tiling": tiling}
     # (3) snapshot storage vs the FP64 oracle gradient
     n, nt = 64, 400
     w = W.config_3d(n, 12.5, 8, nt, nrec_side=32)
