@@ -301,10 +301,7 @@ inline StageLayout stage_layout(int r, int tile, int mt_bytes, bool grad, bool e
 // Fewest pipeline stages of a tile: the halo plane of plane x stays staged
 // until x is updated while planes up to x + r are read ahead, unless the
 // centre values come in tiles of their own (then any two stages pipeline).
-inline int min_stages(int r, int tile, bool grad) {
-  (void)grad;
-  return kTiles[tile].ca ? 2 : r + 2;
-}
+inline int min_stages(int r, int tile) { return kTiles[tile].ca ? 2 : r + 2; }
 
 // Dynamic shared memory of a launch: the stages of both rings, their full
 // and empty barriers, the consumers' unit-tail barrier and 128 bytes of

@@ -529,7 +529,7 @@ static int max_stages(const Plan& pl, int tile) {
   const StageLayout L = stage_layout(pl.r, tile, 4, false, true);
   const int cap = device_smem_optin(pl.device) - 1024;  // static shared memory and slack
   int s = 2 * pl.r + 8;
-  while (s > min_stages(pl.r, tile, false) && (int)smem_bytes(L, s) > cap) --s;
+  while (s > min_stages(pl.r, tile) && (int)smem_bytes(L, s) > cap) --s;
   return s;
 }
 
@@ -545,7 +545,7 @@ static void choose_default_tiling(Plan& pl) {
   const int ms = max_stages(pl, pl.tile);
   const int st_def = kTiles[pl.tile].ca ? (pl.r > 4 ? 5 : 4) : pl.r + 4;
   pl.stages = pl.stages_req > 0 ? std::min(pl.stages_req, ms) : std::min(st_def, ms);
-  if (pl.stages < min_stages(pl.r, pl.tile, false))
+  if (pl.stages < min_stages(pl.r, pl.tile))
     fail(FDW_ERR_ARG, "pipeline too shallow for this order");
   if (pl.lx_req > 0) {
     pl.lx = pl.lx_req;
@@ -900,7 +900,7 @@ static int grad_stages(Plan& pl) {
   const void* fn = step_fn(pl.r, pl.tile, true);
   const int threads = (kTiles[pl.tile].warps + 1) * 32;
   const int cap = device_smem_optin(pl.device) - 1024;
-  const int lo = min_stages(pl.r, pl.tile, true);
+  const int lo = min_stages(pl.r, pl.tile);
   int best = lo, best_nb = -1;
   for (int st = lo; st <= 2 * pl.r + 8 && (int)smem_bytes(L, st) <= cap; ++st) {
     const size_t smem = launch_smem(pl, pl.tile, L, st, fn, threads);
@@ -2548,7 +2548,7 @@ fdw_status fdw_set_tiling(fdw_ctx* c, int tile, int xchunk, int stages) {
   return guard(&c->err, [&] {
     if (tile < -1 || tile >= kNumTiles) fail(FDW_ERR_ARG, "tile index out of range");
     if (xchunk < 0 || stages < 0) fail(FDW_ERR_ARG, "negative tiling value");
-    if (stages > 0 && stages < min_stages(c->r, tile < 0 ? 0 : tile, false))
+    if (stages > 0 && stages < min_stages(c->r, tile < 0 ? 0 : tile))
       fail(FDW_ERR_ARG, "stages must be >= r + 2 (>= 2 for tile 9)");
     c->tile = tile;
     c->xchunk = xchunk;
