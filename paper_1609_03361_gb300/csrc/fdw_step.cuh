@@ -35,6 +35,13 @@
 // A plane is written once (two 16-byte stores) when it arrives, and nothing
 // shifts: the register queue costs 2r moves per point and plane, and 2r+1
 // live registers per point.
+// With CA each stage holds exactly what one update reads: the halo plane x,
+// the tiles of plane x and a separate centre tile of plane x + r (the values
+// that join the queue), after 2r stages of centre tiles that fill the queue;
+// a stage is freed as soon as its plane is updated, so two stages already
+// pipeline (otherwise the stages of planes x .. x + r stay staged while
+// plane x is updated).  CA also forms the neighbour pair sums of two points
+// per instruction (correctly rounded, the scalar sums), to save registers.
 #pragma once
 
 #include <cstdio>
