@@ -225,11 +225,15 @@ __global__ void inject_kernel(const ShotDesc* shots, const InjNode* nodes, const
     const ShotDesc& d = shots[node_shot[i]];
     const float* A = d.inj_a + (long long)row * d.inj_ld;
     const float* B = diff ? d.inj_b + (long long)row * d.inj_ld : nullptr;
+    // the terms in order, the first one from the node record itself
     float sum = 0.f;
-    for (int t = nd.tbeg; t < nd.tend; ++t) {
-      const InjTerm tm = terms[t];
-      const float v = B ? A[tm.j] - B[tm.j] : A[tm.j];
-      sum = fmaf(tm.w, v, sum);
+    if (nd.tend > nd.tbeg) {
+      sum = fmaf(nd.w0, B ? A[nd.j0] - B[nd.j0] : A[nd.j0], sum);
+      for (int t = nd.tbeg + 1; t < nd.tend; ++t) {
+        const InjTerm tm = terms[t];
+        const float v = B ? A[tm.j] - B[tm.j] : A[tm.j];
+        sum = fmaf(tm.w, v, sum);
+      }
     }
     const long long off = ((long long)nd.x * d.ny + nd.y) * d.nzp + nd.z;
     const float sv = load_m(d.m, d.mtype, off);

@@ -221,6 +221,8 @@ inline int group_corners(Corner* c, int n, int U, InjNode* nodes, InjTerm* terms
       nd.y = e.y;
       nd.z = e.z;
       nd.tbeg = i;
+      nd.j0 = e.j;
+      nd.w0 = e.w;
       inj_ptr[e.unit + 1]++;
     }
     nodes[nn - 1].tend = i + 1;

@@ -1387,6 +1387,8 @@ static void build_tb(Plan& pl) {
       nd.tbeg = (int)terms.size();
       for (const InjTerm& t : kv.second) terms.push_back(t);
       nd.tend = (int)terms.size();
+      nd.j0 = kv.second.front().j;
+      nd.w0 = kv.second.front().w;
       nodes.push_back(nd);
       ptr[std::get<0>(kv.first) + 1]++;
     }

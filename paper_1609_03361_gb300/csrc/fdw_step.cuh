@@ -836,12 +836,16 @@ step_kernel(const __grid_constant__ StepParams P) {
         const float* etafp = d->etaf;
         float* accp = d->acc;
         const float* fwdp = GRAD ? d->fwd + (long long)P.fslot * d->fslot : nullptr;
+        // the terms in order, the first one from the node record itself
         auto node_sum = [&](const InjNode& nd) {
           float sum = 0.f;
-          for (int t = nd.tbeg; t < nd.tend; ++t) {
-            const InjTerm tm = terms[t];
-            const float v = B ? A[tm.j] - B[tm.j] : A[tm.j];
-            sum = fmaf(tm.w, v, sum);
+          if (nd.tend > nd.tbeg) {
+            sum = fmaf(nd.w0, B ? A[nd.j0] - B[nd.j0] : A[nd.j0], sum);
+            for (int t = nd.tbeg + 1; t < nd.tend; ++t) {
+              const InjTerm tm = terms[t];
+              const float v = B ? A[tm.j] - B[tm.j] : A[tm.j];
+              sum = fmaf(tm.w, v, sum);
+            }
           }
           return sum;
         };

@@ -85,7 +85,9 @@ enum UnitFlags : int { kUnitUndamped = 1 };
 struct InjNode {
   int x, y, z;
   int tbeg, tend;      // terms [tbeg, tend) in the term array
-  int pad[3];
+  int j0;              // the first term (terms[tbeg]) again, so that a sum
+  float w0;            // needs no term load before its first data load
+  int pad;
 };
 
 struct InjTerm {
